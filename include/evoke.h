@@ -1,0 +1,136 @@
+/*
+ * evoke.h -- C ABI of libevoke, a GB300 (sm_103a) implementation of EVOKE's
+ * per-vertex orbit counting (Pashanasangi & Seshadhri, "Efficiently Counting
+ * Vertex Orbits of All 5-vertex Subgraphs, by EVOKE").
+ *
+ * For every vertex u of a simple undirected graph the library computes the
+ * exact induced counts of the 73 vertex orbits 0..72 of the connected 2- to
+ * 5-vertex patterns H0..H29 (Sec. 1.1 "Problem Description", Fig.
+ * node_orbits): out[u*73 + k] is the number of vertex sets S containing u,
+ * |S| <= 5, whose induced subgraph is the pattern owning orbit k with u in
+ * orbit k.  The route is the paper's: base-pattern counts over the degree
+ * ordered DAG (Sec. 2 "Degree ordering", Thm. running-time), the non-induced
+ * counts of Lem. 4vertexorbit, Lem. 4edgeorbit, Thm. 5vertexorbit and
+ * Thm. 5-Cycle-Clique, then the induced transform DIM = A^-1 DM (App. A).
+ *
+ * Conventions for every entry point:
+ *  - Graph input is CSR in DEVICE memory: rowptr[n+1] (uint32, rowptr[0] = 0,
+ *    rowptr[n] = 2m) and colidx[2m] (uint32).  Each row must be strictly
+ *    increasing, without self-loops, and the graph symmetric (a simple
+ *    undirected graph; Sec. 2).  n < 2^32 - 1 and 2m < 2^32.  Isolated
+ *    vertices and n = 0 are legal.
+ *  - `stream` is a cudaStream_t (0 = legacy default stream).  Work is
+ *    enqueued on it; the functions synchronise that stream internally where
+ *    noted (to size internal buffers and to read validation results) and
+ *    return after the results are written, unless stated otherwise.
+ *  - The caller owns every buffer passed in.  The library allocates its
+ *    internal workspace with cudaMallocAsync on `stream` and frees it before
+ *    returning.
+ *  - Return value: EVOKE_OK or one of the error codes below; nothing throws
+ *    across the ABI.  evoke_strerror() names a code.
+ *  - Counts are int64 two's-complement; the arithmetic wraps modulo 2^64,
+ *    so results are exact whenever the true counts fit in int64.
+ */
+#ifndef EVOKE_H
+#define EVOKE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EVOKE_OK 0
+#define EVOKE_EINVAL 1       /* bad argument (null pointer, sizes inconsistent) */
+#define EVOKE_ENOTSIMPLE 2   /* input is not a simple undirected graph (validate) */
+#define EVOKE_ERANGE 3       /* a vertex id >= n (validate) or n / m too large */
+#define EVOKE_ENOMEM 4       /* internal device allocation failed */
+#define EVOKE_ECUDA 5        /* a CUDA call or kernel launch failed */
+#define EVOKE_ETIMEOUT 6     /* a bounded device wait gave up */
+#define EVOKE_EOVERFLOW 7    /* reserved: checked-arithmetic builds */
+
+typedef struct evoke_opts {
+  int32_t validate;   /* nonzero: check the CSR invariants first (syncs the stream) */
+  int32_t root_ctas;  /* persistent CTAs of the per-root pass; 0 = 2 per SM */
+  int32_t schedule;   /* 0 = degree-bucket schedule (decreasing wedge work) */
+  int32_t reserved;
+} evoke_opts;
+
+/*
+ * evoke_count_orbits -- induced orbit counts of all vertices.
+ *   rowptr, colidx : device CSR as described above (read only).
+ *   n, m           : vertices and undirected edges (colidx has 2m entries).
+ *   out            : device int64[n*73], row-major, orbit index = the
+ *                    paper's orbit number (Fig. node_orbits); fully written.
+ *   opts           : may be NULL (defaults: no validation, 2 CTAs per SM).
+ * Synchronises `stream` (buffer sizing).  Errors: EVOKE_EINVAL (null
+ * pointers with n > 0, rowptr[n] != 2m), EVOKE_ENOTSIMPLE / EVOKE_ERANGE
+ * (validate only), EVOKE_ENOMEM, EVOKE_ECUDA.
+ */
+int evoke_count_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                       int64_t* out, const evoke_opts* opts, void* stream);
+
+/*
+ * evoke_build_dag -- the degree-ordered DAG of Sec. 2: edge u -> v iff
+ * d(u) < d(v), or d(u) = d(v) and u < v.
+ *   dag_rowptr : device uint32[n+1] (written), dag_colidx : device
+ *   uint32[m] (written), out-neighbours of each vertex ascending by id.
+ * Synchronises `stream`.  Errors as evoke_count_orbits.
+ */
+int evoke_build_dag(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                    uint32_t* dag_rowptr, uint32_t* dag_colidx, void* stream);
+
+/*
+ * evoke_edge_orbits -- per-edge counts of Lem. 4edgeorbit and Thm. 4orbit,
+ * one entry per CSR slot s (slot of v in row u, 0 <= s < 2m), device int64[2m]
+ * each (any may be NULL to skip):
+ *   tri[s] = T(u,v) = E1, c4[s] = C4(u,v) = E5, k4[s] = K4(u,v) = E11,
+ *   e7[s] = E7(u,v) = sum over x in N(u)^N(v) of (d(x)-2),
+ *   e9[s] = E9<u,v> = sum over x in N(u)^N(v) of (T(u,x)-1).
+ * Synchronises `stream`.  Errors as evoke_count_orbits.
+ */
+int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                      int64_t* tri, int64_t* c4, int64_t* k4, int64_t* e7, int64_t* e9,
+                      void* stream);
+
+/*
+ * evoke_orbit_matrix -- the library's matrix A of App. A (DM = A * DIM),
+ * derived from the patterns at load time, into HOST int64[73*73] row-major.
+ * Errors: EVOKE_EINVAL (null), EVOKE_ECUDA (pattern tables inconsistent).
+ */
+int evoke_orbit_matrix(int64_t* A);
+
+/*
+ * Phase profiling.  While enabled, every pass of the entry points above is
+ * bracketed by CUDA events recorded on the stream the pass's kernels are
+ * launched on (the caller's stream).  evoke_profile_read() synchronises those
+ * events and returns, per pass name, the number of kernel launches, the
+ * number of executions and the summed device time in milliseconds (host
+ * array `out` of `cap` entries; *count receives the number of passes).
+ * evoke_launch_count() returns the kernels launched by the library since it
+ * was loaded (counted whether or not profiling is enabled).
+ */
+typedef struct evoke_phase_time {
+  char name[24];
+  int32_t launches;
+  int32_t calls;
+  double ms;
+} evoke_phase_time;
+
+int evoke_profile_enable(int on);
+int evoke_profile_read(evoke_phase_time* out, int cap, int* count);
+int evoke_profile_reset(void);
+uint64_t evoke_launch_count(void);
+
+/* Human-readable name of a status code (static string). */
+const char* evoke_strerror(int code);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int evoke_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVOKE_H */

@@ -1,0 +1,14 @@
+"""GB300-native (sm_103a) per-vertex orbit counting of all connected 2- to
+5-vertex graphlets, after EVOKE (Pashanasangi & Seshadhri).
+
+Public API (CUDA only; no CPU fallback):
+    count_orbits(rowptr, colidx, n, m)  -> int64 [n, 73] induced orbit counts
+    edge_orbits(rowptr, colidx, n, m)   -> per-edge T, C4, K4, E7, E9
+    build_dag(rowptr, colidx, n, m)     -> degree-ordered DAG
+    orbit_matrix()                      -> the 73x73 matrix A (DM = A DIM)
+"""
+from ._lib import (EvokeError, build_dag, count_orbits, edge_orbits, load, orbit_matrix,
+                   to_device, version)
+
+__all__ = ["EvokeError", "build_dag", "count_orbits", "edge_orbits", "load", "orbit_matrix",
+           "to_device", "version"]

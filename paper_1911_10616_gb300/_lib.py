@@ -1,0 +1,198 @@
+"""ctypes binding of libevoke (include/evoke.h).  Argument marshalling only:
+every step of the orbit-counting path runs in the library's CUDA kernels.
+There is no CPU fallback: if the library is not built or no GPU is present,
+the calls raise."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+EVOKE_OK = 0
+NORB = 73
+
+_ERRORS = {
+    1: "EVOKE_EINVAL", 2: "EVOKE_ENOTSIMPLE", 3: "EVOKE_ERANGE", 4: "EVOKE_ENOMEM",
+    5: "EVOKE_ECUDA", 6: "EVOKE_ETIMEOUT", 7: "EVOKE_EOVERFLOW",
+}
+
+# exported symbols of include/evoke.h
+SYMBOLS = ("evoke_count_orbits", "evoke_build_dag", "evoke_edge_orbits", "evoke_orbit_matrix",
+           "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
+           "evoke_launch_count", "evoke_strerror", "evoke_version")
+
+
+class EvokeError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_ERRORS.get(code, code)} ({strerror(code)})")
+
+
+class PhaseTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32),
+                ("calls", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
+class EvokeOpts(ctypes.Structure):
+    _fields_ = [("validate", ctypes.c_int32), ("root_ctas", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libevoke.so (building it first if asked and needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libevoke is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        lib.evoke_count_orbits.argtypes = [vp, vp, u32, u64, vp, ctypes.POINTER(EvokeOpts), vp]
+        lib.evoke_count_orbits.restype = ctypes.c_int
+        lib.evoke_build_dag.argtypes = [vp, vp, u32, u64, vp, vp, vp]
+        lib.evoke_build_dag.restype = ctypes.c_int
+        lib.evoke_edge_orbits.argtypes = [vp, vp, u32, u64, vp, vp, vp, vp, vp, vp]
+        lib.evoke_edge_orbits.restype = ctypes.c_int
+        lib.evoke_orbit_matrix.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+        lib.evoke_orbit_matrix.restype = ctypes.c_int
+        lib.evoke_strerror.argtypes = [ctypes.c_int]
+        lib.evoke_strerror.restype = ctypes.c_char_p
+        lib.evoke_version.restype = ctypes.c_int
+        lib.evoke_profile_enable.argtypes = [ctypes.c_int]
+        lib.evoke_profile_read.argtypes = [ctypes.POINTER(PhaseTime), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int)]
+        lib.evoke_launch_count.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load(False).evoke_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def _check(rc: int, what: str):
+    if rc != EVOKE_OK:
+        raise EvokeError(rc, what)
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def to_device(graph, device="cuda"):
+    """Upload a graphgen.Graph as (rowptr, colidx) uint32 bit patterns held in
+    int32 tensors on `device`."""
+    import torch
+    rp = np.ascontiguousarray(graph.rowptr.astype(np.uint32)).view(np.int32)
+    col = np.ascontiguousarray(graph.col.astype(np.uint32)).view(np.int32)
+    return (torch.from_numpy(rp).to(device, non_blocking=False),
+            torch.from_numpy(col).to(device, non_blocking=False))
+
+
+def _check_graph(rowptr, colidx, n):
+    import torch
+    if not (rowptr.is_cuda and colidx.is_cuda):
+        raise ValueError("rowptr / colidx must be CUDA tensors")
+    if rowptr.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)) or \
+            colidx.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise ValueError("rowptr / colidx must hold 32-bit ids")
+    if rowptr.numel() != n + 1 or not rowptr.is_contiguous() or not colidx.is_contiguous():
+        raise ValueError("rowptr must be contiguous with n+1 entries")
+
+
+def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = False,
+                 root_ctas: int = 0, stream=None):
+    """Induced orbit counts, int64 tensor [n, 73] on the graph's device."""
+    import torch
+    _check_graph(rowptr, colidx, n)
+    if out is None:
+        out = torch.empty((n, NORB), dtype=torch.int64, device=rowptr.device)
+    elif out.dtype != torch.int64 or out.numel() != n * NORB or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int64 tensor with n*73 entries")
+    opts = EvokeOpts(1 if validate else 0, int(root_ctas), 0, 0)
+    rc = load().evoke_count_orbits(_ptr(rowptr), _ptr(colidx), n, m, _ptr(out),
+                                   ctypes.byref(opts), _stream_handle(stream))
+    _check(rc, "evoke_count_orbits")
+    return out
+
+
+def edge_orbits(rowptr, colidx, n: int, m: int, stream=None):
+    """Per-slot T, C4, K4, E7, E9<u,v> as int64 tensors of 2m entries."""
+    import torch
+    _check_graph(rowptr, colidx, n)
+    outs = [torch.empty(2 * m, dtype=torch.int64, device=rowptr.device) for _ in range(5)]
+    if m == 0:
+        return dict(zip(["T", "C4", "K4", "E7", "E9"], outs))
+    rc = load().evoke_edge_orbits(_ptr(rowptr), _ptr(colidx), n, m, *[_ptr(o) for o in outs],
+                                  _stream_handle(stream))
+    _check(rc, "evoke_edge_orbits")
+    return dict(zip(["T", "C4", "K4", "E7", "E9"], outs))
+
+
+def build_dag(rowptr, colidx, n: int, m: int, stream=None):
+    import torch
+    _check_graph(rowptr, colidx, n)
+    dp = torch.empty(n + 1, dtype=torch.int32, device=rowptr.device)
+    dc = torch.empty(max(m, 1), dtype=torch.int32, device=rowptr.device)
+    rc = load().evoke_build_dag(_ptr(rowptr), _ptr(colidx), n, m, _ptr(dp), _ptr(dc),
+                                _stream_handle(stream))
+    _check(rc, "evoke_build_dag")
+    return dp, dc[:m]
+
+
+def orbit_matrix() -> np.ndarray:
+    A = np.zeros(73 * 73, dtype=np.int64)
+    _check(load().evoke_orbit_matrix(A.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "evoke_orbit_matrix")
+    return A.reshape(73, 73)
+
+
+def version() -> int:
+    return int(load().evoke_version())
+
+
+def profile_enable(on: bool = True):
+    load().evoke_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().evoke_profile_reset()
+
+
+def profile_read():
+    """{phase: (launches, calls, total_ms)} of the phases run while enabled."""
+    lib = load()
+    cap = 64
+    arr = (PhaseTime * cap)()
+    cnt = ctypes.c_int(0)
+    _check(lib.evoke_profile_read(arr, cap, ctypes.byref(cnt)), "evoke_profile_read")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].calls, arr[i].ms)
+            for i in range(min(cnt.value, cap))}
+
+
+def launch_count() -> int:
+    return int(load().evoke_launch_count())

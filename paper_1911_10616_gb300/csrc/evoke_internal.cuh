@@ -1,0 +1,201 @@
+// Internal declarations shared by the translation units of libevoke (the CUDA
+// path).  Nothing here is part of the public C ABI (include/evoke.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ---------------------------------------------------------------------------
+// Per-vertex accumulators (int64, wrapping arithmetic), structure of arrays:
+// acc[A_xxx * n + u].  Each entry is one partial sum of the equations of
+// Lem. 4vertexorbit / Thm. 5vertexorbit, named after the orbit it feeds.
+// ---------------------------------------------------------------------------
+enum AccIndex : int {
+  A_T = 0,     // T(u): triangles at u
+  A_DM1,       // sum_{v in N(u)} (d(v)-1)
+  A_DM6,       // sum C(d(v)-1, 2)
+  A_DM10,      // sum T(u,v) (d(v)-2)
+  A_DM13,      // sum C(T(u,v), 2)
+  A_S22,       // sum C(d(v)-1, 3)
+  A_S41,       // sum C(T(u,v),2) (d(v)-3)
+  A_S55,       // sum C(T(u,v),3)
+  A_S12,       // opposite-edge sum of (T(v,x)-1), each triangle twice
+  A_S54,       // opposite-edge sum of C(T(v,x)-1, 2), twice
+  A_S46,       // opposite-edge sum of E7(v,x), twice
+  A_S52,       // opposite-edge sum of E5(v,x), twice
+  A_S59,       // opposite-edge sum of E9<v,x> + E9<x,v>, twice
+  A_S65,       // opposite-edge sum of E11(v,x) = K4(v,x), twice
+  A_S70,       // sum over 4-cliques at u of (K4(opposite triangle) - 1)
+  A_S66,       // sum over 4-cliques at u of T-sum of the opposite triangle
+  A_S71,       // sum over triangles at u of C(K4(t), 2)
+  A_DM8,       // C4(u)
+  A_S36,       // sum_v C(W(u,v),2) (d(v)-2)
+  A_S50,       // sum_v C(W(u,v),3)
+  A_S51,       // sum_v TT(u,v) (W(u,v)-1)
+  A_S63,       // sum_v D(u,v) (W(u,v)-2)
+  A_C5,        // 5-cycles through u
+  A_K5,        // 5-cliques through u
+  A_S4,        // sum DM1(v)
+  A_S9,        // sum (T(v) - T(u,v))
+  A_S18,       // sum DM6(v)
+  A_S19,       // sum DM5(v)
+  A_S24,       // sum DM10(v)
+  A_S28,       // sum T(v)
+  A_S31,       // sum (d(v)-1) T(v)
+  A_S35,       // sum DM8(v)
+  A_S37,       // sum E5(u,v) (d(v)-2)
+  A_S39,       // sum DM13(v)
+  A_S40,       // sum E9<v,u> (d(v)-3)
+  A_S45,       // sum DM12(v)
+  A_S57,       // sum E11(u,v) (d(v)-3)
+  A_S60,       // sum E9<v,u> (T(u,v)-1)
+  A_S67,       // sum E11(u,v) (T(u,v)-2)
+  A_K4X3,      // sum E11(u,v) = 3 K4(u)
+  A_S29,       // sum T(u,v) DM1(v)
+  A_S32,       // sum T(u,v) C(d(v)-2, 2)
+  A_S43,       // sum T(u,v) (T(v)-1)
+  A_S48,       // sum (T(u,v)-1) E7(u,v)
+  A_S61,       // sum (T(u,v)-1) E9<u,v>   (twice the triangle sum)
+  A_S53,       // sum T(u,v) E5(u,v)
+  A_S25,       // sum (d(v)-2) E7(u,v)      (twice the triangle sum)
+  A_S49,       // sum over neighbour pairs of C(W(v,x)-1, 2)
+  A_S62,       // sum over neighbour pairs of D(v,x)
+  A_S64,       // sum over diamonds with chord at u of (W(v,x)-2)
+  A_S68,       // sum over v in N(u) of 4-cycles through u inside N(v)
+  A_S69X4,     // 4 * (4-cycles inside N(u))
+  A_DM4,       // DM4(u)  (stored for the next neighbour round)
+  A_DM9,       // DM9(u)
+  A_DM12,      // DM12(u)
+  A_DM14,      // DM14(u)
+  A_S15,       // sum DM4(v)
+  A_S27,       // sum DM9(v)
+  A_S56,       // sum DM14(v)
+  A_WORK,      // root work estimate sum_{v in N(u)} d(v) (scheduling)
+  NACC
+};
+
+// per-slot arrays (slot s = position of v in row u of the CSR, 0..2m-1)
+struct SlotArrays {
+  u32* T;        // T(u,v)
+  u64* E5;       // C4(u,v)
+  u64* E7;       // sum_{x in T(u,v)} (d(x)-2)
+  u64* E9;       // E9<u,v> = sum_{x in T(u,v)} (T(u,x)-1)
+  u64* K4;       // K4(u,v) = E11
+  u64* b49;      // root u's share of DM49 for centre v
+  u64* b62;      // root u's share of DM62 for centre v
+  u64* b64;      // root u's share of DM64 for chord end v
+  u64* b68;      // 4-cycles through v inside N(u)
+  u64* bc5;      // root u's 5-cycle credits for v
+};
+
+struct Graph {
+  u32 n;
+  u64 S;                 // 2m slots
+  const u32* rowptr;     // n+1
+  const u32* col;        // S
+  u32* deg;              // n
+  u32* rev;              // S: slot of (v,u) for slot (u,v)
+  u32* dag_ptr;          // n+1: out-neighbours (u -> v iff u precedes v)
+  u32* dag_col;          // m
+  u32* dag_slot;         // m: CSR slot of each DAG edge (in the source row)
+  u64* tl_ptr;           // S+1: triangle-list offsets per slot
+  u32* tl;               // per slot (u,v): slots (u,x) for x in N(u)^N(v), ascending x
+};
+
+// device helpers ------------------------------------------------------------
+__device__ __forceinline__ bool prec(const u32* deg, u32 i, u32 j) {
+  u32 di = deg[i], dj = deg[j];
+  return di < dj || (di == dj && i < j);
+}
+
+__device__ __forceinline__ u64 c2(long long x) {
+  if (x < 2) return 0;
+  unsigned __int128 p = (unsigned __int128)x * (unsigned __int128)(x - 1);
+  return (u64)(p >> 1);
+}
+__device__ __forceinline__ u64 c3(long long x) {
+  if (x < 3) return 0;
+  unsigned __int128 p = (unsigned __int128)x * (unsigned __int128)(x - 1) * (unsigned __int128)(x - 2);
+  return (u64)(p / 6);
+}
+__device__ __forceinline__ u64 c4(long long x) {
+  if (x < 4) return 0;
+  unsigned __int128 p = (unsigned __int128)x * (unsigned __int128)(x - 1);
+  p = p * (unsigned __int128)(x - 2);
+  p = p / 6;
+  p = p * (unsigned __int128)(x - 3);
+  return (u64)(p / 4);
+}
+// binomial of a count that may already exceed 2^32 (e.g. C(DM1, 2))
+__device__ __forceinline__ u64 c2u(u64 x) {
+  if ((long long)x < 2) return 0;
+  unsigned __int128 p = (unsigned __int128)x * (unsigned __int128)(x - 1);
+  return (u64)(p >> 1);
+}
+
+// first index i in [lo, hi) with a[i] >= key
+__device__ __forceinline__ u32 lower_bound_u32(const u32* a, u32 lo, u32 hi, u32 key) {
+  while (lo < hi) {
+    u32 mid = lo + ((hi - lo) >> 1);
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ bool contains_u32(const u32* a, u32 lo, u32 hi, u32 key) {
+  u32 p = lower_bound_u32(a, lo, hi, key);
+  return p < hi && a[p] == key;
+}
+
+__device__ __forceinline__ u64 warp_sum(u64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// status word bits written by kernels (read back by the host)
+enum DeviceStatus : int {
+  ST_OK = 0,
+  ST_NOT_SIMPLE = 1,   // unsorted row, duplicate, self-loop or asymmetric edge
+  ST_RANGE = 2,        // vertex id >= n
+};
+
+// launchers (one per kernel family), all asynchronous on `st`
+void launch_degrees(const Graph& g, cudaStream_t st);
+void launch_rev_validate(const Graph& g, int* status, cudaStream_t st);
+void launch_dag(const Graph& g, u32* tmp_counts, void* scan_tmp, cudaStream_t st);
+void launch_scan_u32_to_u64(const u32* in, u64* out, u64 count, void* tmp, cudaStream_t st);
+size_t scan_tmp_bytes(u64 count);
+void launch_scan_u32_inplace(u32* data, u64 count, void* tmp, cudaStream_t st);
+void launch_tri_count(const Graph& g, u32* T, cudaStream_t st);
+void launch_tri_fill(const Graph& g, const u32* T, cudaStream_t st);
+void launch_tri_edge(const Graph& g, const SlotArrays& sa, cudaStream_t st);
+void launch_vsum1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+void launch_tri_opp1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+struct RootScratch {
+  u32* W;        // per CTA: n   (bit 31 flags a neighbour of the root)
+  u32* Wn;       // per CTA: n   non in-in wedges
+  u32* D;        // per CTA: n   diamonds with the root off the chord
+  u32* P;        // per CTA: n   directed 3-paths ending at the root
+  u64* TT;       // per CTA: n   sum of T(x,v) over wedges root-x-v
+  u32* touched;  // per CTA: n
+  u32* order;    // n: roots in schedule order
+  u32* head;     // 1: queue head
+  u32* bucket_cnt;  // 64
+  int ctas;
+};
+size_t root_scratch_bytes(u32 n, int ctas);
+void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
+void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
+                           u32* pref, u32 pref_stride, cudaStream_t st);
+void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
+                 cudaStream_t st);
+void launch_k5(const Graph& g, u64* acc, cudaStream_t st);
+void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);
+int upload_transform(const long long* A73x73);
+void launch_finalize(const Graph& g, const u64* acc, long long* out, cudaStream_t st);

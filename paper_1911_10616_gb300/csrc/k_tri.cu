@@ -1,0 +1,231 @@
+// Triangle layer (Thm. 4orbit): per-edge triangle counts T(e) and sorted
+// per-edge triangle lists, the triangle-based edge orbits E7 and E9 of
+// Lem. 4edgeorbit, per-vertex sums over the edge opposite a vertex in its
+// triangles, and the per-triangle 4-clique counts K4(t) that feed E11 = K4(e),
+// and orbits 66, 70 and 71 of Thm. 5vertexorbit.
+//
+// Triangle lists: for the slot s of edge (u,v) in row u, tl[tl_ptr[s] ..
+// tl_ptr[s+1]) holds, in ascending order of x, the slot of (u,x) in row u for
+// every common neighbour x.  The list of the reverse slot holds the slots of
+// (v,x) in row v in the same order, so index k of both lists names the same
+// triangle {u,v,x}.
+#include "evoke_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ u32 row_of(const u32* rowptr, u32 n, u32 s) {
+  // largest u with rowptr[u] <= s
+  u32 lo = 0, hi = n;
+  while (hi - lo > 1) {
+    u32 mid = lo + ((hi - lo) >> 1);
+    if (rowptr[mid] <= s) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// one thread per DAG edge (u -> v): u precedes v, so d(u) <= d(v); walk N(u)
+// and binary-search each entry in N(v).
+template <bool kFill>
+__global__ void tri_kernel(Graph g, u32* __restrict__ T, u32 m) {
+  const u32 e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const u32 s = g.dag_slot[e];
+  const u32 u = row_of(g.rowptr, g.n, s);
+  const u32 v = g.col[s];
+  const u32 ub = g.rowptr[u], ue = g.rowptr[u + 1];
+  const u32 vb = g.rowptr[v], ve = g.rowptr[v + 1];
+  const u32 r = g.rev[s];
+  u32 cnt = 0;
+  u64 o1 = 0, o2 = 0;
+  if (kFill) {
+    o1 = g.tl_ptr[s];
+    o2 = g.tl_ptr[r];
+  }
+  u32 lo = vb;
+  for (u32 i = ub; i < ue; ++i) {
+    const u32 x = g.col[i];
+    lo = lower_bound_u32(g.col, lo, ve, x);
+    if (lo >= ve) break;
+    if (g.col[lo] == x) {
+      if (kFill) {
+        g.tl[o1 + cnt] = i;
+        g.tl[o2 + cnt] = lo;
+      }
+      ++cnt;
+    }
+  }
+  if (!kFill) {
+    T[s] = cnt;
+    T[r] = cnt;
+  }
+}
+
+// per slot: E7(u,v) = sum_{x in T(u,v)} (d(x)-2);  E9<u,v> = sum (T(u,x)-1)
+__global__ void tri_edge_kernel(Graph g, SlotArrays sa) {
+  const u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.S) return;
+  u64 e7 = 0, e9 = 0;
+  for (u64 k = g.tl_ptr[s]; k < g.tl_ptr[s + 1]; ++k) {
+    const u32 sx = g.tl[k];
+    e7 += (u64)((long long)g.deg[g.col[sx]] - 2);
+    e9 += (u64)((long long)sa.T[sx] - 1);
+  }
+  sa.E7[s] = e7;
+  sa.E9[s] = e9;
+}
+
+// per vertex u: sums over the edges (v,x) opposite u in its triangles, each
+// triangle visited twice (through v and through x).
+template <int kPass>
+__global__ void tri_opp_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
+  const u32 u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (u >= g.n) return;
+  const u32 n = g.n;
+  u64 a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  for (u32 s = g.rowptr[u]; s < g.rowptr[u + 1]; ++s) {
+    if (sa.T[s] == 0) continue;
+    const u32 r = g.rev[s];
+    for (u64 k = g.tl_ptr[r] + lane; k < g.tl_ptr[r + 1]; k += 32) {
+      const u32 e = g.tl[k];  // slot (v,x) in row v
+      if (kPass == 1) {
+        const long long t = sa.T[e];
+        a0 += (u64)(t - 1);
+        a1 += c2(t - 1);
+      } else {
+        a0 += sa.E7[e];
+        a1 += sa.E5[e];
+        a2 += sa.E9[e] + sa.E9[g.rev[e]];
+        a3 += sa.K4[e];
+      }
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  if (kPass == 2) {
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+  }
+  if (lane == 0) {
+    if (kPass == 1) {
+      acc[(u64)A_S12 * n + u] = a0;
+      acc[(u64)A_S54 * n + u] = a1;
+    } else {
+      acc[(u64)A_S46 * n + u] = a0;
+      acc[(u64)A_S52 * n + u] = a1;
+      acc[(u64)A_S59 * n + u] = a2;
+      acc[(u64)A_S65 * n + u] = a3;
+    }
+  }
+}
+
+// one thread per triangle-list entry; the entry (slot (a,b), x = c) is the
+// triangle's single representative when a precedes b precedes c.  Then
+// K4(t) = |N(a)^N(b)^N(c)| = |tl(a,b) ^ tl(a,c)| (both ascending slot lists).
+__global__ void k4_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, u64 total) {
+  const u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  // slot owning entry q
+  u64 lo = 0, hi = g.S;
+  while (hi - lo > 1) {
+    u64 mid = lo + ((hi - lo) >> 1);
+    if (g.tl_ptr[mid] <= q) lo = mid;
+    else hi = mid;
+  }
+  const u32 s = (u32)lo;
+  const u32 a = row_of(g.rowptr, g.n, s);
+  const u32 b = g.col[s];
+  if (!prec(g.deg, a, b)) return;
+  const u32 sac = g.tl[q];
+  const u32 c = g.col[sac];
+  if (!prec(g.deg, b, c)) return;
+  const u32 r = g.rev[s];
+  const u32 sbc = g.tl[g.tl_ptr[r] + (q - g.tl_ptr[s])];
+  // merge-intersect tl(a,b) and tl(a,c)
+  const u64 p0 = g.tl_ptr[s], p1 = g.tl_ptr[s + 1];
+  const u64 q0 = g.tl_ptr[sac], q1 = g.tl_ptr[sac + 1];
+  u64 i = p0, j = q0;
+  u32 k4 = 0;
+  while (i < p1 && j < q1) {
+    const u32 x = g.tl[i], y = g.tl[j];
+    if (x < y) ++i;
+    else if (y < x) ++j;
+    else { ++k4; ++i; ++j; }
+  }
+  if (!k4) return;
+  const u32 n = g.n;
+  atomicAdd(&sa.K4[s], (u64)k4);
+  atomicAdd(&sa.K4[r], (u64)k4);
+  atomicAdd(&sa.K4[sac], (u64)k4);
+  atomicAdd(&sa.K4[g.rev[sac]], (u64)k4);
+  atomicAdd(&sa.K4[sbc], (u64)k4);
+  atomicAdd(&sa.K4[g.rev[sbc]], (u64)k4);
+  const u64 k2 = c2(k4);
+  if (k2) {
+    atomicAdd(&acc[(u64)A_S71 * n + a], k2);
+    atomicAdd(&acc[(u64)A_S71 * n + b], k2);
+    atomicAdd(&acc[(u64)A_S71 * n + c], k2);
+  }
+  const u64 tsum = (u64)sa.T[s] + sa.T[sac] + sa.T[sbc];
+  i = p0;
+  j = q0;
+  while (i < p1 && j < q1) {
+    const u32 x = g.tl[i], y = g.tl[j];
+    if (x < y) ++i;
+    else if (y < x) ++j;
+    else {
+      const u32 apex = g.col[x];
+      if (k4 > 1) atomicAdd(&acc[(u64)A_S70 * n + apex], (u64)(k4 - 1));
+      atomicAdd(&acc[(u64)A_S66 * n + apex], tsum);
+      ++i;
+      ++j;
+    }
+  }
+}
+
+// every 4-clique on an edge lies in two of the edge's triangles
+__global__ void halve_kernel(u64* __restrict__ x, u64 count) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) x[i] >>= 1;
+}
+
+inline unsigned blocks_for(u64 threads, unsigned bs) { return (unsigned)((threads + bs - 1) / bs); }
+
+}  // namespace
+
+void launch_tri_count(const Graph& g, u32* T, cudaStream_t st) {
+  const u32 m = (u32)(g.S / 2);
+  if (!m) return;
+  tri_kernel<false><<<blocks_for(m, 256), 256, 0, st>>>(g, T, m);
+}
+
+void launch_tri_fill(const Graph& g, const u32* T, cudaStream_t st) {
+  const u32 m = (u32)(g.S / 2);
+  if (!m) return;
+  tri_kernel<true><<<blocks_for(m, 256), 256, 0, st>>>(g, const_cast<u32*>(T), m);
+}
+
+void launch_tri_edge(const Graph& g, const SlotArrays& sa, cudaStream_t st) {
+  if (!g.S) return;
+  tri_edge_kernel<<<blocks_for(g.S, 256), 256, 0, st>>>(g, sa);
+}
+
+void launch_tri_opp1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {
+  if (!g.n) return;
+  tri_opp_kernel<1><<<blocks_for((u64)g.n * 32, 256), 256, 0, st>>>(g, sa, acc);
+}
+
+void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {
+  if (!g.n) return;
+  tri_opp_kernel<2><<<blocks_for((u64)g.n * 32, 256), 256, 0, st>>>(g, sa, acc);
+}
+
+void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {
+  if (!g.S) return;
+  u64 total = 0;
+  cudaMemcpyAsync(&total, g.tl_ptr + g.S, sizeof(u64), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (total) k4_kernel<<<blocks_for(total, 256), 256, 0, st>>>(g, sa, acc, total);
+  halve_kernel<<<blocks_for(g.S, 256), 256, 0, st>>>(sa.K4, g.S);
+}
