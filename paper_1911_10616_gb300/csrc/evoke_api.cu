@@ -288,11 +288,19 @@ size_t sz(size_t count) {
   return ((std::max<size_t>(count, 1) * sizeof(T)) + 255) & ~size_t(255);
 }
 
-__global__ void dmax_kernel(const u32* deg, u32 n, u32* out) {
+// out[0] = max degree, out[1] = max DAG out-degree
+__global__ void dmax_kernel(const u32* deg, const u32* dag_ptr, u32 n, u32* out) {
   u32 u = blockIdx.x * blockDim.x + threadIdx.x;
   u32 v = u < n ? deg[u] : 0;
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
+  u32 w = u < n ? dag_ptr[u + 1] - dag_ptr[u] : 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (v) atomicMax(out, v);
+    if (w) atomicMax(out + 1, w);
+  }
 }
 
 __global__ void widen_kernel(const u32* in, long long* out, u64 count) {
@@ -317,6 +325,7 @@ struct Run {
   void* block2 = nullptr;
   cudaStream_t st = nullptr;
   u32 dmax = 0;
+  u32 max_outdeg = 0;
   u64 ntri_entries = 0;
 };
 
@@ -375,18 +384,19 @@ int prepare(Run& R, const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, 
   }
   phase("dag", n ? 5 : 0, st, [&] { launch_dag(g, R.cnt, R.scan_tmp, st); });
   phase("dmax", n ? 1 : 0, st, [&] {
-    if (n) dmax_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.deg, n, R.misc);
+    if (n) dmax_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.deg, g.dag_ptr, n, R.misc);
   });
   if (!need_lists) return EVOKE_OK;
   phase("tri_count", m ? 1 : 0, st, [&] { launch_tri_count(g, R.sa.T, st); });
   phase("tri_scan", S ? 3 : 0, st, [&] { launch_scan_u32_to_u64(R.sa.T, g.tl_ptr, S, R.scan_tmp, st); });
   u64 total = 0;
-  u32 dmax = 0;
+  u32 mx[2] = {0, 0};
   cudaMemcpyAsync(&total, g.tl_ptr + S, sizeof(u64), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&dmax, R.misc, sizeof(u32), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(mx, R.misc, 2 * sizeof(u32), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
   R.ntri_entries = total;
-  R.dmax = dmax;
+  R.dmax = mx[0];
+  R.max_outdeg = mx[1];
   if (cudaMallocAsync(&R.block2, sz<u32>(total), st) != cudaSuccess) return EVOKE_ENOMEM;
   g.tl = static_cast<u32*>(R.block2);
   phase("tri_fill", m ? 1 : 0, st, [&] { launch_tri_fill(g, R.sa.T, st); });
@@ -516,7 +526,11 @@ int run_all(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t
   const u32 link_warps = (u32)sm_count() * 64;  // multiple of 8
   const u32 pref_stride = dmax + 1;
   // second arena: slot arrays, accumulators, scratch
-  size_t bytes = 9 * sz<u64>(S) + sz<u64>((size_t)NACC * n) +
+  const bool root_profile = [] {
+    const char* e = getenv("EVOKE_ROOT_PROFILE");
+    return e && *e && *e != '0';
+  }();
+  size_t bytes = 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) + sz<u64>((size_t)NACC * n) +
                  root_scratch_bytes(n, ctas) + 256 * 8 + sz<u32>(n) + sz<u32>(64) + sz<u32>(4) +
                  sz<u32>((size_t)ctas * pref_stride) + sz<u32>((size_t)link_warps * dmax);
   void* blk = nullptr;
@@ -535,15 +549,17 @@ int run_all(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t
   u64* acc = ar.take<u64>((size_t)NACC * n);
   RootScratch rs{};
   rs.ctas = ctas;
-  rs.W = ar.take<u32>((size_t)ctas * n);
-  rs.Wn = ar.take<u32>((size_t)ctas * n);
-  rs.D = ar.take<u32>((size_t)ctas * n);
-  rs.P = ar.take<u32>((size_t)ctas * n);
-  rs.TT = ar.take<u64>((size_t)ctas * n);
+  rs.map = ar.take<MapRec>((size_t)ctas * n);
   rs.touched = ar.take<u32>((size_t)ctas * n);
+  rs.jlist = ar.take<u32>((size_t)ctas * n);
   rs.order = ar.take<u32>(n);
   rs.bucket_cnt = ar.take<u32>(64);
   rs.head = ar.take<u32>(4);
+  rs.tsrc = acc + (size_t)A_TSRC * n;
+  rs.prof = root_profile ? ar.take<u64>(8) : nullptr;
+  rs.cycles = nullptr;
+  sa.Mmid = ar.take<u32>(S);
+  sa.Mtop = ar.take<u32>(S);
   u32* pref = ar.take<u32>((size_t)ctas * pref_stride);
   u32* link_scratch = ar.take<u32>((size_t)link_warps * dmax);
   if (ar.overflow) {
@@ -560,8 +576,16 @@ int run_all(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t
   phase("k4", (R.ntri_entries ? 1 : 0) + sl, st, [&] { launch_k4(g, sa, acc, st); });
   phase("schedule", 3 * nl, st, [&] { launch_schedule(g, acc, rs, st); });
   phase("root", nl, st, [&] { launch_root_with_pref(g, sa, acc, rs, pref, pref_stride, st); });
+  if (rs.prof) {
+    u64 pc[8] = {};
+    cudaMemcpyAsync(pc, rs.prof, sizeof(pc), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    fprintf(stderr, "evoke root phases (Gcycles summed over CTAs): wedges %.2f, diamonds+R %.2f, "
+                    "3-path push %.2f, wedges2+k %.2f, scan %.2f\n",
+            pc[0] * 1e-9, pc[1] * 1e-9, pc[2] * 1e-9, pc[3] * 1e-9, pc[4] * 1e-9);
+  }
   phase("link", sl, st, [&] { launch_link(g, sa, link_scratch, link_warps, dmax, st); });
-  phase("k5", sl, st, [&] { launch_k5(g, acc, st); });
+  phase("k5", sl, st, [&] { launch_k5(g, acc, R.max_outdeg, st); });
   phase("tri_opp2", nl, st, [&] { launch_tri_opp2(g, sa, acc, st); });
   phase("vsum2", nl, st, [&] { launch_vsum2(g, sa, acc, st); });
   phase("vsum3", nl, st, [&] { launch_vsum3(g, acc, st); });

@@ -73,6 +73,7 @@ enum AccIndex : int {
   A_S27,       // sum DM9(v)
   A_S56,       // sum DM14(v)
   A_WORK,      // root work estimate sum_{v in N(u)} d(v) (scheduling)
+  A_TSRC,      // DAG triangles with u as the source (u precedes both others)
   NACC
 };
 
@@ -88,6 +89,8 @@ struct SlotArrays {
   u64* b64;      // root u's share of DM64 for chord end v
   u64* b68;      // 4-cycles through v inside N(u)
   u64* bc5;      // root u's 5-cycle credits for v
+  u32* Mmid;     // triangles on (u,v) whose third vertex lies between u and v
+  u32* Mtop;     // triangles on (u,v) whose third vertex follows both
 };
 
 struct Graph {
@@ -175,16 +178,31 @@ void launch_tri_edge(const Graph& g, const SlotArrays& sa, cudaStream_t st);
 void launch_vsum1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_tri_opp1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+// one record per vertex id in a CTA's dense 2-hop map (64 bytes: the fields
+// a root touches for one vertex share a pair of 32-byte sectors)
+struct __align__(64) MapRec {
+  u32 W;      // |N(root) ^ N(x)|, bit 31 flags a neighbour of the root
+  u32 Wn;     // wedges root-v-x not in-in at v (not root->v<-x)
+  u32 D;      // diamonds with root and x off the chord
+  u32 X;      // sum over k in N-(root)^N-(x) of #(k -> y -> x)
+  u64 TT;     // sum over wedges root-v-x of T(v,x)
+  u64 P;      // directed 3-paths root <- k -> j -> x
+  u64 RY;     // (|N-(root)^N-(x)| << 32) | sum over those k of #(k -> x -> y, k -> y)
+  u64 Pjl;    // those 3-paths with j ~ root
+  u64 Z;      // sum of Wn over N+(x)
+  u64 pad;
+};
+
 struct RootScratch {
-  u32* W;        // per CTA: n   (bit 31 flags a neighbour of the root)
-  u32* Wn;       // per CTA: n   non in-in wedges
-  u32* D;        // per CTA: n   diamonds with the root off the chord
-  u32* P;        // per CTA: n   directed 3-paths ending at the root
-  u64* TT;       // per CTA: n   sum of T(x,v) over wedges root-x-v
-  u32* touched;  // per CTA: n
+  MapRec* map;   // per CTA: n records, zero between roots
+  u32* touched;  // per CTA: n, ids touched by the current root
+  u32* jlist;    // per CTA: n, middle vertices of the current root's 3-paths
   u32* order;    // n: roots in schedule order
   u32* head;     // 1: queue head
   u32* bucket_cnt;  // 64
+  u64* tsrc;     // n: DAG triangles with the vertex as source
+  u64* prof;     // optional [8]: cycles per phase (summed over roots)
+  u64* cycles;   // optional [n]: cycles per root
   int ctas;
 };
 size_t root_scratch_bytes(u32 n, int ctas);
@@ -193,7 +211,7 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
                            u32* pref, u32 pref_stride, cudaStream_t st);
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
                  cudaStream_t st);
-void launch_k5(const Graph& g, u64* acc, cudaStream_t st);
+void launch_k5(const Graph& g, u64* acc, u32 max_outdeg, cudaStream_t st);
 void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);

@@ -112,33 +112,38 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
             u32 pref_stride) {
   const u32 n = g.n;
   const u64 off = (u64)blockIdx.x * n;
-  u32* __restrict__ W = rs.W + off;
-  u32* __restrict__ Wn = rs.Wn + off;
-  u32* __restrict__ D = rs.D + off;
-  u32* __restrict__ P = rs.P + off;
-  u64* __restrict__ TT = rs.TT + off;
+  MapRec* __restrict__ M = rs.map + off;
   u32* __restrict__ touched = rs.touched + off;
+  u32* __restrict__ jlist = rs.jlist + off;
+  __shared__ u32 s_wpref[kRootThreads / 32][33];
+  __shared__ u32 s_wsab[kRootThreads / 32][32];
+  __shared__ u32 s_wsa[kRootThreads / 32][32];
+  __shared__ u32 s_wsb[kRootThreads / 32][32];
   u32* pref = pref_all + (u64)blockIdx.x * pref_stride;
-  __shared__ u32 s_root, s_nt, s_carry;
+  __shared__ u32 s_root, s_nt, s_nj, s_carry;
   __shared__ u64 s_red[32];
+  __shared__ long long s_t0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
   for (;;) {
     if (threadIdx.x == 0) {
       s_root = atomicAdd(rs.head, 1u);
       s_nt = 0;
+      s_nj = 0;
+      s_t0 = clock64();
     }
     __syncthreads();
     const u32 qi = s_root;
     if (qi >= n) break;
     const u32 u = rs.order[qi];
     const u32 ub = g.rowptr[u], ue = g.rowptr[u + 1], du = ue - ub;
-    const u32 degu = du;
+    long long tp = 0;
+    if (rs.prof && threadIdx.x == 0) tp = clock64();
 
     // phase 0: mark the neighbours, prefix of their degrees
     for (u32 i = threadIdx.x; i < du; i += blockDim.x) {
       const u32 v = g.col[ub + i];
-      W[v] = kFlag;
+      M[v].W = kFlag;
       touched[atomicAdd(&s_nt, 1u)] = v;
     }
     neighbour_degree_prefix(g, ub, du, pref, s_red, &s_carry);
@@ -151,77 +156,137 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 t = g.rowptr[v] + (w - pref[i]);
       const u32 x = g.col[t];
       if (x == u) continue;
-      const u32 old = atomicAdd(&W[x], 1u);
+      const u32 old = atomicAdd(&M[x].W, 1u);
       if (old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
-      if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) atomicAdd(&Wn[x], 1u);
-      atomicAdd(&TT[x], (u64)sa.T[t]);
+      if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) atomicAdd(&M[x].Wn, 1u);
+      atomicAdd(&M[x].TT, (u64)sa.T[t]);
     }
     __syncthreads();
+    if (rs.prof && threadIdx.x == 0) {
+      long long t = clock64();
+      atomicAdd(&rs.prof[0], (u64)(t - tp));
+      tp = t;
+    }
 
     // phase 2a: diamonds.  Triangle (u,a,b) with a < b; every y in
-    // N(a)^N(b) other than u closes a diamond with chord (a,b).
+    // N(a)^N(b) other than u closes a diamond with chord (a,b).  Each warp
+    // takes 32 triangle-list entries of u at a time and walks the
+    // concatenation of their chord lists, one list entry per lane.
     {
       const u64 q0 = g.tl_ptr[ub], q1 = g.tl_ptr[ue];
-      for (u64 q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        // owning slot of entry q within row u
-        u32 lo = ub, hi = ue;
-        while (hi - lo > 1) {
-          u32 mid = lo + ((hi - lo) >> 1);
-          if (g.tl_ptr[mid] <= q) lo = mid;
-          else hi = mid;
+      const u64 span = q1 - q0;
+      for (u64 base = (u64)wid * 32; base < span; base += (u64)nw * 32) {
+        const u64 q = q0 + base + lane;
+        u32 len = 0, sab = 0, sa_ = 0, sb = 0;
+        if (q < q1) {
+          u32 lo = ub, hi = ue;
+          while (hi - lo > 1) {
+            u32 mid = lo + ((hi - lo) >> 1);
+            if (g.tl_ptr[mid] <= q) lo = mid;
+            else hi = mid;
+          }
+          sb = g.tl[q];
+          sa_ = lo;
+          if (sb > lo) {  // b > a, each triangle at u once
+            sab = g.tl[g.tl_ptr[g.rev[lo]] + (q - g.tl_ptr[lo])];
+            len = (u32)(g.tl_ptr[sab + 1] - g.tl_ptr[sab]);
+          }
         }
-        const u32 s = lo;
-        const u32 sb = g.tl[q];
-        if (sb <= s) continue;  // b > a, each triangle at u once
-        const u32 sab = g.tl[g.tl_ptr[g.rev[s]] + (q - g.tl_ptr[s])];
-        u64 add64 = 0;
-        for (u64 k = g.tl_ptr[sab]; k < g.tl_ptr[sab + 1]; ++k) {
-          const u32 y = g.col[g.tl[k]];
+        s_wsa[wid][lane] = sa_;
+        s_wsb[wid][lane] = sb;
+        // inclusive prefix of the list lengths across the warp
+        u32 incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        s_wpref[wid][lane + 1] = incl;
+        if (lane == 0) s_wpref[wid][0] = 0;
+        s_wsab[wid][lane] = sab;
+        __syncwarp();
+        const u32 tot = s_wpref[wid][32];
+        for (u32 it = lane; it < tot; it += 32) {
+          // owning triangle: largest t with pref[t] <= it
+          u32 lo = 0, hi = 32;
+          while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (s_wpref[wid][mid] <= it) lo = mid;
+            else hi = mid;
+          }
+          const u32 tsab = s_wsab[wid][lo];
+          const u32 y = g.col[g.tl[g.tl_ptr[tsab] + (it - s_wpref[wid][lo])]];
           if (y == u) continue;
-          atomicAdd(&D[y], 1u);
-          if (u < y) add64 += (u64)((long long)(W[y] & kCnt) - 2);
+          atomicAdd(&M[y].D, 1u);
+          if (u < y) {
+            const u64 add = (u64)((long long)(M[y].W & kCnt) - 2);
+            if (add) {  // chord ends: slots (u,a), (u,b) of this triangle
+              atomicAdd(&sa.b64[s_wsa[wid][lo]], add);
+              atomicAdd(&sa.b64[s_wsb[wid][lo]], add);
+            }
+          }
         }
-        if (add64) {
-          atomicAdd(&sa.b64[s], add64);
-          atomicAdd(&sa.b64[sb], add64);
-        }
+        __syncwarp();
       }
     }
-    // phase 2b: directed 3-paths u <- k -> j -> i  (Fig. 5cycle, l = u)
-    {
-      u64 cl = 0;
-      for (u32 idx = wid; idx < du; idx += nw) {
-        const u32 k = g.col[ub + idx];
-        if (!prec(g.deg, k, u)) continue;  // need k -> u
-        const u32 kb = g.dag_ptr[k], ke = g.dag_ptr[k + 1];
-        u64 ck = 0;
-        for (u32 p = kb + lane; p < ke; p += 32) {
-          const u32 j = g.dag_col[p];
-          if (j == u) continue;
-          const u32 jl = (W[j] & kFlag) ? 1u : 0u;
-          u64 cj = 0;
-          for (u32 p2 = g.dag_ptr[j]; p2 < g.dag_ptr[j + 1]; ++p2) {
-            const u32 i = g.dag_col[p2];
-            if (i == u) continue;
-            const u32 wn = Wn[i];
-            if (!wn) continue;
-            const u32 ik = contains_u32(g.dag_col, kb, ke, i) ? 1u : 0u;
-            const u64 c = (u64)(wn - ik - jl);
-            cl += c;
-            ck += c - ik;
-            cj += c - jl;
-            if (c) atomicAdd(&acc[(u64)A_C5 * n + i], c);
-            atomicAdd(&P[i], 1u);
-          }
-          if (cj) atomicAdd(&acc[(u64)A_C5 * n + j], cj);
-        }
-        ck = warp_sum(ck);
-        if (lane == 0 && ck) atomicAdd(&sa.bc5[ub + idx], ck);
+    // phase 2b: directed 3-paths u <- k -> j -> i (Fig. 5cycle with l = u),
+    // grouped by the middle vertex j:  R[j] = |N-(u) ^ N-(j)| (out-out
+    // wedges u <- k -> j), Y[j] = sum over those k of the triangles k->j->x
+    // with k->x, X[x] = sum over k in N-(u) ^ N-(x) of the triangles k->y->x.
+    for (u32 idx = wid; idx < du; idx += nw) {
+      const u32 k = g.col[ub + idx];
+      if (!prec(g.deg, k, u)) continue;  // k -> u
+      for (u32 p = g.dag_ptr[k] + lane; p < g.dag_ptr[k + 1]; p += 32) {
+        const u32 x = g.dag_col[p];
+        if (x == u) continue;
+        const u32 sk = g.dag_slot[p];
+        const u64 old = atomicAdd(&M[x].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
+        if ((old >> 32) == 0) jlist[atomicAdd(&s_nj, 1u)] = x;
+        const u32 mm = sa.Mmid[sk];
+        if (mm) atomicAdd(&M[x].X, mm);
       }
-      cl = block_sum(cl, s_red);
-      if (threadIdx.x == 0 && cl) atomicAdd(&acc[(u64)A_C5 * n + u], cl);
     }
     __syncthreads();
+    if (rs.prof && threadIdx.x == 0) {
+      long long t = clock64();
+      atomicAdd(&rs.prof[1], (u64)(t - tp));
+      tp = t;
+    }
+    // phase 2c: per middle vertex j, push R[j] to every end i in N+(j) (the
+    // 3-path counts P) and pull Z[j] = sum of Wn over N+(j); credit j.
+    {
+      const u32 nj = s_nj;
+      for (u32 idx = wid; idx < nj; idx += nw) {
+        const u32 j = jlist[idx];
+        const u64 ry = M[j].RY;
+        const u64 R = ry >> 32, Yj = ry & 0xffffffffull;
+        const bool jl = (M[j].W & kFlag) != 0;
+        const bool j_to_u = jl && prec(g.deg, j, u);
+        u64 z = 0;
+        for (u32 p = g.dag_ptr[j] + lane; p < g.dag_ptr[j + 1]; p += 32) {
+          const u32 i = g.dag_col[p];
+          if (i == u) continue;
+          const u32 wn = M[i].Wn;
+          if (!wn) continue;
+          z += wn;
+          atomicAdd(&M[i].P, R);
+          if (jl) atomicAdd(&M[i].Pjl, R);
+        }
+        z = warp_sum(z);
+        if (lane == 0) {
+          M[j].Z = z;
+          const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (j_to_u ? 1 : 0);
+          const u64 cj = R * z - Yj + (j_to_u ? R : 0) - (jl ? 2 * R * dpj : 0);
+          if (cj) atomicAdd(&acc[(u64)A_C5 * n + j], cj);
+        }
+      }
+    }
+    __syncthreads();
+    if (rs.prof && threadIdx.x == 0) {
+      long long t = clock64();
+      atomicAdd(&rs.prof[2], (u64)(t - tp));
+      tp = t;
+    }
 
     // phase 3a: wedges again, now that W, D and P are complete
     {
@@ -239,13 +304,13 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (x == u) {
             valid = false;
           } else {
-            const long long wx = W[x] & kCnt;
+            const long long wx = M[x].W & kCnt;
             e5 = (u64)(wx - 1);
             if (u < x) {
               b49 = c2(wx - 1);
-              b62 = D[x];
+              b62 = M[x].D;
             }
-            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = P[x];
+            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = M[x].P;
           }
         }
         seg_atomic_add(sa.E5, s, valid, e5);
@@ -254,28 +319,61 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         seg_atomic_add(sa.bc5, s, valid, bw);
       }
     }
+    // phase 3a': 5-cycle credit of each in-neighbour k (the source vertex)
+    for (u32 idx = wid; idx < du; idx += nw) {
+      const u32 k = g.col[ub + idx];
+      if (!prec(g.deg, k, u)) continue;
+      u64 zs = 0;
+      for (u32 p = g.dag_ptr[k] + lane; p < g.dag_ptr[k + 1]; p += 32) {
+        const u32 j = g.dag_col[p];
+        if (j == u) continue;
+        u64 t = M[j].Z;
+        if (M[j].W & kFlag) {
+          const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (prec(g.deg, j, u) ? 1 : 0);
+          t -= dpj;
+        }
+        zs += t;
+      }
+      zs = warp_sum(zs);
+      if (lane == 0) {
+        const u32 rk = g.rev[ub + idx];  // slot of u in row k (a DAG slot)
+        const u64 tri = rs.tsrc[k] - sa.Mtop[rk] - sa.Mmid[rk];
+        const u64 ck = zs - 2 * tri;
+        if (ck) atomicAdd(&sa.bc5[ub + idx], ck);
+      }
+    }
     __syncthreads();
+    if (rs.prof && threadIdx.x == 0) {
+      long long t = clock64();
+      atomicAdd(&rs.prof[3], (u64)(t - tp));
+      tp = t;
+    }
 
-    // phase 3b: scan the map, reset it
+    // phase 3b: scan the map (orbits 8, 36, 50, 51, 63; the 5-cycle credits of
+    // the path ends), reset it
     {
-      u64 a8 = 0, a36 = 0, a50 = 0, a51 = 0, a63 = 0;
+      u64 a8 = 0, a36 = 0, a50 = 0, a51 = 0, a63 = 0, a5 = 0;
       const u32 nt = s_nt;
       for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
         const u32 x = touched[idx];
-        const u32 wr = W[x];
+        MapRec r = M[x];
+        const u32 wr = r.W;
         const long long w = wr & kCnt;
         const u64 cw2 = c2(w);
         a8 += cw2;
         a36 += cw2 * (u64)((long long)g.deg[x] - 2);
         a50 += c3(w);
-        const u64 tt = TT[x] - ((wr & kFlag) ? (u64)w : 0);
+        const u64 tt = r.TT - ((wr & kFlag) ? (u64)w : 0);
         a51 += tt * (u64)(w - 1);
-        a63 += (u64)D[x] * (u64)(w - 2);
-        W[x] = 0;
-        Wn[x] = 0;
-        D[x] = 0;
-        P[x] = 0;
-        TT[x] = 0;
+        a63 += (u64)r.D * (u64)(w - 2);
+        if (r.P | r.X) {
+          const bool u_to_x = (wr & kFlag) && prec(g.deg, u, x);
+          const u64 rx = r.RY >> 32;
+          const u64 ci = r.P * (u64)r.Wn - ((u64)r.X - (u_to_x ? rx : 0)) - r.Pjl;
+          if (ci) atomicAdd(&acc[(u64)A_C5 * n + x], ci);
+          a5 += ci;
+        }
+        M[x] = MapRec{};
       }
       a8 = block_sum(a8, s_red);
       if (threadIdx.x == 0) acc[(u64)A_DM8 * n + u] = a8;
@@ -287,9 +385,15 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       if (threadIdx.x == 0) acc[(u64)A_S51 * n + u] = a51;
       a63 = block_sum(a63, s_red);
       if (threadIdx.x == 0) acc[(u64)A_S63 * n + u] = a63;
+      a5 = block_sum(a5, s_red);
+      if (threadIdx.x == 0 && a5) atomicAdd(&acc[(u64)A_C5 * n + u], a5);
     }
-    (void)degu;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      if (rs.prof) atomicAdd(&rs.prof[4], (u64)(t - tp));
+      if (rs.cycles) rs.cycles[u] = (u64)(t - s_t0);
+    }
   }
 }
 
@@ -355,31 +459,24 @@ __global__ void link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u
   }
 }
 
-// --- 5-cliques: per DAG edge (a -> b), triangles inside N+(a)^N+(b) --------
-__global__ void k5_kernel(Graph g, u64* __restrict__ acc, u32 m) {
-  const u32 e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m) return;
-  // source of DAG edge e
-  u32 lo = 0, hi = g.n;
-  while (hi - lo > 1) {
-    u32 mid = lo + ((hi - lo) >> 1);
-    if (g.dag_ptr[mid] <= e) lo = mid;
-    else hi = mid;
-  }
-  const u32 a = lo, b = g.dag_col[e];
+// --- 5-cliques: per DAG edge (a -> b), triangles inside S = N+(a)^N+(b) ----
+// Every 5-clique a<b<c<d<e (DAG order) is seen once, at its lowest edge (a,b),
+// as the triangle {c,d,e} of G[S].  One warp per DAG edge: S goes to shared
+// memory (ascending ids), the adjacency inside S to bitmap rows, and the
+// triangles of G[S] through c are sum_{d in row(c)} popc(row(c) & row(d)) / 2.
+// Edges whose S exceeds the shared-memory capacity take a slower path that
+// re-derives S on the fly.
+constexpr int kK5Warps = 4;
+
+__device__ void k5_slow_edge(const Graph& g, u64* acc, u32 a, u32 b) {
+  const int lane = threadIdx.x & 31;
+  const u32 n = g.n;
   const u32 ab = g.dag_ptr[a], ae = g.dag_ptr[a + 1];
   const u32 bb = g.dag_ptr[b], be = g.dag_ptr[b + 1];
-  if (ae - ab < 3 || be - bb < 3) return;
-  const u32 n = g.n;
   u64 cab = 0;
-  u32 i = ab, j = bb;
-  while (i < ae && j < be) {
-    const u32 x = g.dag_col[i], y = g.dag_col[j];
-    if (x < y) { ++i; continue; }
-    if (y < x) { ++j; continue; }
-    const u32 c = x;
-    ++i;
-    ++j;
+  for (u32 i = ab + lane; i < ae; i += 32) {
+    const u32 c = g.dag_col[i];
+    if (!contains_u32(g.dag_col, bb, be, c)) continue;
     u64 cc = 0;
     const u32 cb = g.dag_ptr[c], ce = g.dag_ptr[c + 1];
     for (u32 p = cb; p < ce; ++p) {
@@ -400,16 +497,103 @@ __global__ void k5_kernel(Graph g, u64* __restrict__ acc, u32 m) {
     if (cc) atomicAdd(&acc[(u64)A_K5 * n + c], cc);
     cab += cc;
   }
-  if (cab) {
+  cab = warp_sum(cab);
+  if (lane == 0 && cab) {
     atomicAdd(&acc[(u64)A_K5 * n + a], cab);
     atomicAdd(&acc[(u64)A_K5 * n + b], cab);
+  }
+}
+
+__global__ void __launch_bounds__(kK5Warps * 32)
+k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
+  extern __shared__ u32 k5_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 words = (smax + 31) / 32;
+  u32* S = k5_smem + (size_t)wid * (smax + (size_t)smax * words);
+  u32* rows = S + smax;
+  const u32 n = g.n;
+  const u32 gw = blockIdx.x * kK5Warps + wid;
+  const u32 nw = gridDim.x * kK5Warps;
+  for (u32 e = gw; e < m; e += nw) {
+    // source of DAG edge e
+    u32 lo = 0, hi = g.n;
+    while (hi - lo > 1) {
+      u32 mid = lo + ((hi - lo) >> 1);
+      if (g.dag_ptr[mid] <= e) lo = mid;
+      else hi = mid;
+    }
+    const u32 a = lo, b = g.dag_col[e];
+    u32 xb = g.dag_ptr[a], xe = g.dag_ptr[a + 1];
+    u32 yb = g.dag_ptr[b], ye = g.dag_ptr[b + 1];
+    if (xe - xb < 3 || ye - yb < 3) continue;
+    if (xe - xb > ye - yb) {  // walk the shorter list
+      u32 t = xb; xb = yb; yb = t;
+      t = xe; xe = ye; ye = t;
+    }
+    // S = N+(a) ^ N+(b), ascending
+    u32 s = 0;
+    bool over = false;
+    for (u32 base = xb; base < xe; base += 32) {
+      const u32 i = base + lane;
+      const u32 x = i < xe ? g.dag_col[i] : 0;
+      const bool hit = i < xe && contains_u32(g.dag_col, yb, ye, x);
+      const u32 bal = __ballot_sync(0xffffffffu, hit);
+      const u32 pos = s + __popc(bal & ((1u << lane) - 1u));
+      if (hit && pos < smax) S[pos] = x;
+      s += __popc(bal);
+    }
+    if (s < 3) continue;
+    if (s > smax) over = true;
+    if (over) {
+      k5_slow_edge(g, acc, a, b);
+      continue;
+    }
+    const u32 w = (s + 31) / 32;
+    for (u32 i = lane; i < s * w; i += 32) rows[i] = 0;
+    __syncwarp();
+    // adjacency inside S (both directions)
+    for (u32 ci = lane; ci < s; ci += 32) {
+      const u32 c = S[ci];
+      for (u32 p = g.dag_ptr[c]; p < g.dag_ptr[c + 1]; ++p) {
+        const u32 d = g.dag_col[p];
+        const u32 di = lower_bound_u32(S, 0, s, d);
+        if (di < s && S[di] == d) {
+          atomicOr(&rows[ci * w + (di >> 5)], 1u << (di & 31));
+          atomicOr(&rows[di * w + (ci >> 5)], 1u << (ci & 31));
+        }
+      }
+    }
+    __syncwarp();
+    u64 tot = 0;
+    for (u32 ci = lane; ci < s; ci += 32) {
+      const u32* rc = rows + ci * w;
+      u32 t2 = 0;
+      for (u32 k = 0; k < w; ++k) {
+        u32 bits = rc[k];
+        while (bits) {
+          const u32 di = k * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          const u32* rd = rows + di * w;
+          for (u32 q = 0; q < w; ++q) t2 += __popc(rc[q] & rd[q]);
+        }
+      }
+      const u32 tc = t2 >> 1;
+      if (tc) atomicAdd(&acc[(u64)A_K5 * n + S[ci]], (u64)tc);
+      tot += tc;
+    }
+    tot = warp_sum(tot);
+    if (lane == 0 && tot) {
+      atomicAdd(&acc[(u64)A_K5 * n + a], tot / 3);
+      atomicAdd(&acc[(u64)A_K5 * n + b], tot / 3);
+    }
+    __syncwarp();
   }
 }
 
 }  // namespace
 
 size_t root_scratch_bytes(u32 n, int ctas) {
-  return (size_t)ctas * n * (4 * sizeof(u32) + sizeof(u64) + sizeof(u32));
+  return (size_t)ctas * n * (sizeof(MapRec) + 2 * sizeof(u32)) + 16 * 256;
 }
 
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st) {
@@ -434,8 +618,21 @@ void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, 
   link_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(g, sa, scratch, dmax);
 }
 
-void launch_k5(const Graph& g, u64* acc, cudaStream_t st) {
+void launch_k5(const Graph& g, u64* acc, u32 max_outdeg, cudaStream_t st) {
   const u32 m = (u32)(g.S / 2);
-  if (!m) return;
-  k5_kernel<<<(m + 255) / 256, 256, 0, st>>>(g, acc, m);
+  if (!m || max_outdeg < 3) return;
+  // shared memory per warp: S list + |S| x ceil(|S|/32) bitmap words
+  u32 smax = (max_outdeg + 31) / 32 * 32;
+  const u32 cap = 640;
+  if (smax > cap) smax = cap;
+  const size_t per_warp = ((size_t)smax + (size_t)smax * ((smax + 31) / 32)) * sizeof(u32);
+  const size_t smem = per_warp * kK5Warps;
+  cudaFuncSetAttribute(k5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_kernel, kK5Warps * 32, smem);
+  const u32 blocks = (u32)sms * (u32)(per_sm > 0 ? per_sm : 1) * 4;
+  k5_kernel<<<blocks, kK5Warps * 32, smem, st>>>(g, acc, m, smax);
 }

@@ -61,18 +61,30 @@ __global__ void tri_kernel(Graph g, u32* __restrict__ T, u32 m) {
   }
 }
 
-// per slot: E7(u,v) = sum_{x in T(u,v)} (d(x)-2);  E9<u,v> = sum (T(u,x)-1)
+// per slot (u,v): E7(u,v) = sum_{x in T(u,v)} (d(x)-2);  E9<u,v> = sum (T(u,x)-1);
+// and, in DAG order, the triangles whose third vertex x lies between u and v
+// (Mmid) or after both (Mtop).
 __global__ void tri_edge_kernel(Graph g, SlotArrays sa) {
   const u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.S) return;
+  const u32 u = row_of(g.rowptr, g.n, (u32)s);
+  const u32 v = g.col[s];
   u64 e7 = 0, e9 = 0;
+  u32 mid = 0, top = 0;
   for (u64 k = g.tl_ptr[s]; k < g.tl_ptr[s + 1]; ++k) {
     const u32 sx = g.tl[k];
-    e7 += (u64)((long long)g.deg[g.col[sx]] - 2);
+    const u32 x = g.col[sx];
+    e7 += (u64)((long long)g.deg[x] - 2);
     e9 += (u64)((long long)sa.T[sx] - 1);
+    if (prec(g.deg, u, x)) {
+      if (prec(g.deg, x, v)) ++mid;
+      else ++top;
+    }
   }
   sa.E7[s] = e7;
   sa.E9[s] = e9;
+  sa.Mmid[s] = mid;
+  sa.Mtop[s] = top;
 }
 
 // per vertex u: sums over the edges (v,x) opposite u in its triangles, each

@@ -19,9 +19,11 @@ __global__ void vsum1_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   const int lane = threadIdx.x & 31;
   if (u >= g.n) return;
   const u32 n = g.n;
-  u64 t2 = 0, s1 = 0, s6 = 0, s10 = 0, s13 = 0, s22 = 0, s41 = 0, s55 = 0, wk = 0;
+  u64 t2 = 0, s1 = 0, s6 = 0, s10 = 0, s13 = 0, s22 = 0, s41 = 0, s55 = 0, wk = 0, ts = 0;
   for (u32 s = g.rowptr[u] + lane; s < g.rowptr[u + 1]; s += 32) {
-    const long long dv = g.deg[g.col[s]];
+    const u32 v = g.col[s];
+    const long long dv = g.deg[v];
+    if (prec(g.deg, u, v)) ts += sa.Mtop[s];
     const long long t = sa.T[s];
     t2 += (u64)t;
     s1 += sgn(dv - 1);
@@ -36,7 +38,9 @@ __global__ void vsum1_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   t2 = warp_sum(t2); s1 = warp_sum(s1); s6 = warp_sum(s6); s10 = warp_sum(s10);
   s13 = warp_sum(s13); s22 = warp_sum(s22); s41 = warp_sum(s41); s55 = warp_sum(s55);
   wk = warp_sum(wk);
+  ts = warp_sum(ts);
   if (lane == 0) {
+    acc[(u64)A_TSRC * n + u] = ts;
     acc[(u64)A_T * n + u] = t2 >> 1;
     acc[(u64)A_DM1 * n + u] = s1;
     acc[(u64)A_DM6 * n + u] = s6;
