@@ -185,7 +185,7 @@ struct __align__(64) MapRec {
   u32 Wn;     // wedges root-v-x not in-in at v (not root->v<-x)
   u32 D;      // diamonds with root and x off the chord
   u32 X;      // sum over k in N-(root)^N-(x) of #(k -> y -> x)
-  u64 TT;     // sum over wedges root-v-x of T(v,x)
+  u64 spare;
   u64 P;      // directed 3-paths root <- k -> j -> x
   u64 RY;     // (|N-(root)^N-(x)| << 32) | sum over those k of #(k -> x -> y, k -> y)
   u64 Pjl;    // those 3-paths with j ~ root

@@ -107,6 +107,26 @@ __device__ void neighbour_degree_prefix(const Graph& g, u32 ub, u32 du, u32* pre
   __syncthreads();
 }
 
+constexpr u32 kSmemPref = 2048;  // neighbour-degree prefix kept in shared memory up to here
+
+// per-warp segmented sum over runs of equal `key` (non-decreasing across the
+// lanes, 0xffffffff for idle lanes); returns the run total on the run's last
+// lane and sets *is_tail there.
+__device__ __forceinline__ u64 seg_sum(u32 key, u64 val, bool* is_tail) {
+  const int lane = threadIdx.x & 31;
+  const u32 prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const u32 heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  const u32 upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  const int start = 31 - __clz(heads & upto);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 y = __shfl_up_sync(0xffffffffu, val, o);
+    if (lane - o >= start) val += y;
+  }
+  *is_tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  return val;
+}
+
 __global__ void __launch_bounds__(kRootThreads)
 root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* pref_all,
             u32 pref_stride) {
@@ -119,11 +139,12 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
   __shared__ u32 s_wsab[kRootThreads / 32][32];
   __shared__ u32 s_wsa[kRootThreads / 32][32];
   __shared__ u32 s_wsb[kRootThreads / 32][32];
-  u32* pref = pref_all + (u64)blockIdx.x * pref_stride;
+  __shared__ u32 s_pref[kSmemPref + 1];
   __shared__ u32 s_root, s_nt, s_nj, s_carry;
   __shared__ u64 s_red[32];
   __shared__ long long s_t0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u32* gpref = pref_all + (u64)blockIdx.x * pref_stride;
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -137,8 +158,10 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     if (qi >= n) break;
     const u32 u = rs.order[qi];
     const u32 ub = g.rowptr[u], ue = g.rowptr[u + 1], du = ue - ub;
+    u32* pref = du + 1 <= kSmemPref ? s_pref : gpref;
     long long tp = 0;
     if (rs.prof && threadIdx.x == 0) tp = clock64();
+    u64 a51 = 0, a63 = 0;
 
     // phase 0: mark the neighbours, prefix of their degrees
     for (u32 i = threadIdx.x; i < du; i += blockDim.x) {
@@ -149,17 +172,17 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     neighbour_degree_prefix(g, ub, du, pref, s_red, &s_carry);
     const u32 total = pref[du];
 
-    // phase 1: wedges u - v - x
+    // phase 1: wedges u - v - x.  W (low word) and Wn (high word) of the
+    // record are bumped by one 64-bit atomic.
     for (u32 w = threadIdx.x; w < total; w += blockDim.x) {
       const u32 i = seg_find(pref, du + 1, w);
       const u32 v = g.col[ub + i];
       const u32 t = g.rowptr[v] + (w - pref[i]);
       const u32 x = g.col[t];
       if (x == u) continue;
-      const u32 old = atomicAdd(&M[x].W, 1u);
-      if (old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
-      if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) atomicAdd(&M[x].Wn, 1u);
-      atomicAdd(&M[x].TT, (u64)sa.T[t]);
+      const bool in_in = prec(g.deg, u, v) && prec(g.deg, x, v);
+      const u64 old = atomicAdd(reinterpret_cast<u64*>(&M[x].W), in_in ? 1ull : (1ull | (1ull << 32)));
+      if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
     }
     __syncthreads();
     if (rs.prof && threadIdx.x == 0) {
@@ -169,9 +192,9 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     }
 
     // phase 2a: diamonds.  Triangle (u,a,b) with a < b; every y in
-    // N(a)^N(b) other than u closes a diamond with chord (a,b).  Each warp
-    // takes 32 triangle-list entries of u at a time and walks the
-    // concatenation of their chord lists, one list entry per lane.
+    // N(a)^N(b) other than u closes a diamond with chord (a,b) and u, y off
+    // the chord.  Each warp takes 32 triangle-list entries of u at a time and
+    // walks the concatenation of their chord lists, one list entry per lane.
     {
       const u64 q0 = g.tl_ptr[ub], q1 = g.tl_ptr[ue];
       const u64 span = q1 - q0;
@@ -192,9 +215,6 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
             len = (u32)(g.tl_ptr[sab + 1] - g.tl_ptr[sab]);
           }
         }
-        s_wsa[wid][lane] = sa_;
-        s_wsb[wid][lane] = sb;
-        // inclusive prefix of the list lengths across the warp
         u32 incl = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -204,26 +224,38 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         s_wpref[wid][lane + 1] = incl;
         if (lane == 0) s_wpref[wid][0] = 0;
         s_wsab[wid][lane] = sab;
+        s_wsa[wid][lane] = sa_;
+        s_wsb[wid][lane] = sb;
         __syncwarp();
         const u32 tot = s_wpref[wid][32];
-        for (u32 it = lane; it < tot; it += 32) {
-          // owning triangle: largest t with pref[t] <= it
-          u32 lo = 0, hi = 32;
-          while (hi - lo > 1) {
-            const u32 mid = (lo + hi) >> 1;
-            if (s_wpref[wid][mid] <= it) lo = mid;
-            else hi = mid;
-          }
-          const u32 tsab = s_wsab[wid][lo];
-          const u32 y = g.col[g.tl[g.tl_ptr[tsab] + (it - s_wpref[wid][lo])]];
-          if (y == u) continue;
-          atomicAdd(&M[y].D, 1u);
-          if (u < y) {
-            const u64 add = (u64)((long long)(M[y].W & kCnt) - 2);
-            if (add) {  // chord ends: slots (u,a), (u,b) of this triangle
-              atomicAdd(&sa.b64[s_wsa[wid][lo]], add);
-              atomicAdd(&sa.b64[s_wsb[wid][lo]], add);
+        for (u32 it0 = 0; it0 < tot; it0 += 32) {
+          const u32 it = it0 + lane;
+          u32 key = 0xffffffffu;
+          u64 add = 0;
+          if (it < tot) {
+            u32 lo = 0, hi = 32;
+            while (hi - lo > 1) {
+              const u32 mid = (lo + hi) >> 1;
+              if (s_wpref[wid][mid] <= it) lo = mid;
+              else hi = mid;
             }
+            const u32 tsab = s_wsab[wid][lo];
+            const u32 y = g.col[g.tl[g.tl_ptr[tsab] + (it - s_wpref[wid][lo])]];
+            if (y != u) {
+              const u64 wy2 = (u64)((long long)(M[y].W & kCnt) - 2);
+              a63 += wy2;                // DM63: sum over diamonds of W(u,y) - 2
+              if (u < y) {
+                atomicAdd(&M[y].D, 1u);  // D(u,y), needed for y > u only
+                add = wy2;
+                key = lo;
+              }
+            }
+          }
+          bool tail;
+          const u64 sum = seg_sum(key, add, &tail);
+          if (tail && key != 0xffffffffu && sum) {  // orbit-64 shares of the chord ends
+            atomicAdd(&sa.b64[s_wsa[wid][key]], sum);
+            atomicAdd(&sa.b64[s_wsb[wid][key]], sum);
           }
         }
         __syncwarp();
@@ -288,7 +320,9 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       tp = t;
     }
 
-    // phase 3a: wedges again, now that W, D and P are complete
+    // phase 3a: wedges again, now that W, D and P are complete: E5 = C4(u,v),
+    // orbit-49/62 shares of the centre, 5-cycle credit of the wedge centre,
+    // and DM51 = sum over wedges u-v-x of (T(v,x) - [u~x]) (W(u,x) - 1).
     {
       const u32 iters = (total + blockDim.x - 1) / blockDim.x * blockDim.x;
       for (u32 w = threadIdx.x; w < iters; w += blockDim.x) {
@@ -304,8 +338,10 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (x == u) {
             valid = false;
           } else {
-            const long long wx = M[x].W & kCnt;
+            const u32 wr = M[x].W;
+            const long long wx = wr & kCnt;
             e5 = (u64)(wx - 1);
+            a51 += ((u64)sa.T[t] - ((wr & kFlag) ? 1 : 0)) * (u64)(wx - 1);
             if (u < x) {
               b49 = c2(wx - 1);
               b62 = M[x].D;
@@ -349,23 +385,20 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       tp = t;
     }
 
-    // phase 3b: scan the map (orbits 8, 36, 50, 51, 63; the 5-cycle credits of
-    // the path ends), reset it
+    // phase 3b: scan the map (orbits 8, 36, 50; the 5-cycle credits of the
+    // path ends), reset it
     {
-      u64 a8 = 0, a36 = 0, a50 = 0, a51 = 0, a63 = 0, a5 = 0;
+      u64 a8 = 0, a36 = 0, a50 = 0, a5 = 0;
       const u32 nt = s_nt;
       for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
         const u32 x = touched[idx];
-        MapRec r = M[x];
+        const MapRec r = M[x];
         const u32 wr = r.W;
         const long long w = wr & kCnt;
         const u64 cw2 = c2(w);
         a8 += cw2;
         a36 += cw2 * (u64)((long long)g.deg[x] - 2);
         a50 += c3(w);
-        const u64 tt = r.TT - ((wr & kFlag) ? (u64)w : 0);
-        a51 += tt * (u64)(w - 1);
-        a63 += (u64)r.D * (u64)(w - 2);
         if (r.P | r.X) {
           const bool u_to_x = (wr & kFlag) && prec(g.deg, u, x);
           const u64 rx = r.RY >> 32;
@@ -420,38 +453,96 @@ __global__ void sched_scatter_kernel(const u64* __restrict__ work, u32 n, u32* c
 }
 
 // --- wheel pass: 4-cycles through a inside N(u), for every slot (u,a) ------
-// sum_c C(W_c, 2) is accumulated as the sum of the counter value before each
-// increment.
-__global__ void link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
-  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const u32 nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  u32* M = scratch + (u64)gw * dmax;
+// (orbits 68 and 69: a wheel is a hub plus a 4-cycle in the hub's
+// neighbourhood).  W_c = number of 2-paths a - b - c inside N(u); the
+// 4-cycles through a are sum_c C(W_c, 2), accumulated as the sum of the
+// counter value before each increment.  One warp per slot (u,a); the warp
+// walks the concatenated triangle lists of the b's 32 at a time.  Counters
+// are 16-bit halves of shared-memory words when d(u) <= kLinkSmem (then
+// W_c < 2^16), else 32-bit words of the warp's global scratch row.
+constexpr int kLinkWarps = 8;
+constexpr u32 kLinkSmem = 2048;
+
+__global__ void __launch_bounds__(kLinkWarps * 32)
+link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
+  __shared__ u32 s_map[kLinkWarps][kLinkSmem / 2];
+  __shared__ u32 s_pref[kLinkWarps][33];
+  __shared__ u32 s_sb[kLinkWarps][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 gw = blockIdx.x * kLinkWarps + wid;
+  const u32 nwarps = gridDim.x * kLinkWarps;
+  u32* gmap = scratch + (u64)gw * dmax;
+  for (u32 i = lane; i < kLinkSmem / 2; i += 32) s_map[wid][i] = 0;
+  __syncwarp();
   for (u64 s = gw; s < g.S; s += nwarps) {
     if (sa.T[s] < 2) continue;
-    const u32 a = g.col[s];
-    (void)a;
-    // row of s: the map is indexed by position in that row
     u32 lo = 0, hi = g.n;
     while (hi - lo > 1) {
       u32 mid = lo + ((hi - lo) >> 1);
       if (g.rowptr[mid] <= (u32)s) lo = mid;
       else hi = mid;
     }
-    const u32 ub = g.rowptr[lo];
+    const u32 ub = g.rowptr[lo], du = g.rowptr[lo + 1] - ub;
+    const bool small = du <= kLinkSmem;
     u64 c4 = 0;
-    for (u64 k = g.tl_ptr[s] + lane; k < g.tl_ptr[s + 1]; k += 32) {
-      const u32 sb = g.tl[k];
-      for (u64 k2 = g.tl_ptr[sb]; k2 < g.tl_ptr[sb + 1]; ++k2) {
-        const u32 sc = g.tl[k2];
-        if (sc == (u32)s) continue;
-        c4 += atomicAdd(&M[sc - ub], 1u);
+    u32 steps = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) {
+        // clear: in bulk when cheaper than walking the lists again
+        if (small && steps >= du / 2) {
+          for (u32 i = lane; i < (du + 1) / 2; i += 32) s_map[wid][i] = 0;
+          break;
+        }
+        if (!small && steps >= du) {
+          for (u32 i = lane; i < du; i += 32) gmap[i] = 0;
+          break;
+        }
       }
-    }
-    __syncwarp();
-    for (u64 k = g.tl_ptr[s] + lane; k < g.tl_ptr[s + 1]; k += 32) {
-      const u32 sb = g.tl[k];
-      for (u64 k2 = g.tl_ptr[sb]; k2 < g.tl_ptr[sb + 1]; ++k2) M[g.tl[k2] - ub] = 0;
+      for (u64 k0 = g.tl_ptr[s]; k0 < g.tl_ptr[s + 1]; k0 += 32) {
+        const u64 k = k0 + lane;
+        u32 sb = 0, len = 0;
+        if (k < g.tl_ptr[s + 1]) {
+          sb = g.tl[k];
+          len = sa.T[sb];
+        }
+        u32 incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        s_pref[wid][lane + 1] = incl;
+        if (lane == 0) s_pref[wid][0] = 0;
+        s_sb[wid][lane] = sb;
+        __syncwarp();
+        const u32 tot = s_pref[wid][32];
+        for (u32 it = lane; it < tot; it += 32) {
+          u32 l2 = 0, h2 = 32;
+          while (h2 - l2 > 1) {
+            const u32 mid = (l2 + h2) >> 1;
+            if (s_pref[wid][mid] <= it) l2 = mid;
+            else h2 = mid;
+          }
+          const u32 sbb = s_sb[wid][l2];
+          const u32 sc = g.tl[g.tl_ptr[sbb] + (it - s_pref[wid][l2])];
+          if (sc == (u32)s) continue;
+          const u32 pc = sc - ub;
+          if (pass == 0) {
+            if (small) {
+              const u32 sh = (pc & 1u) * 16u;
+              c4 += (atomicAdd(&s_map[wid][pc >> 1], 1u << sh) >> sh) & 0xffffu;
+            } else {
+              c4 += atomicAdd(&gmap[pc], 1u);
+            }
+            ++steps;
+          } else {
+            if (small) s_map[wid][pc >> 1] = 0;
+            else gmap[pc] = 0;
+          }
+        }
+        __syncwarp();
+      }
+      if (pass == 0) steps = (u32)warp_sum(steps);
     }
     __syncwarp();
     c4 = warp_sum(c4);
@@ -615,7 +706,7 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
                  cudaStream_t st) {
   if (!g.S || !warps) return;
-  link_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(g, sa, scratch, dmax);
+  link_kernel<<<warps / kLinkWarps, kLinkWarps * 32, 0, st>>>(g, sa, scratch, dmax);
 }
 
 void launch_k5(const Graph& g, u64* acc, u32 max_outdeg, cudaStream_t st) {
