@@ -82,6 +82,30 @@ int evoke_build_dag(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, 
                     uint32_t* dag_rowptr, uint32_t* dag_colidx, void* stream);
 
 /*
+ * evoke_build_dag_noalloc -- the same DAG as evoke_build_dag, for callers
+ * that cannot allocate device memory: for example programs whose GPU memory
+ * is owned up front by their own pool or arena (an allocation by a library
+ * would fail or fragment it), or latency-critical code that cannot afford an
+ * allocation, which may synchronise the device.  It allocates nothing: the
+ * caller passes every buffer, and the one scratch buffer it needs (partial
+ * sums of a prefix sum, about 32 KiB) is a static device array of the
+ * library, held by every GPU that loads the library until the process exits.
+ * The paper has no counterpart; this is an interface convenience.
+ *   rowptr, colidx, n, m : device CSR as above (rowptr[n] must equal 2m; if
+ *                          it does not, writes past m entries are dropped).
+ *   dag_rowptr : device uint32[n+1], dag_colidx : device uint32[m] (written).
+ * Limits: n <= 8,388,608 (EVOKE_ERANGE beyond).  All calls share the static
+ * scratch array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address once; make it before any
+ * stream capture on that device.  Synchronises `stream`.
+ * Errors: EVOKE_EINVAL (null pointers), EVOKE_ERANGE, EVOKE_ECUDA.
+ */
+int evoke_build_dag_noalloc(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n,
+                            uint64_t m, uint32_t* dag_rowptr, uint32_t* dag_colidx,
+                            void* stream);
+
+/*
  * evoke_edge_orbits -- per-edge counts of Lem. 4edgeorbit and Thm. 4orbit,
  * one entry per CSR slot s (slot of v in row u, 0 <= s < 2m), device int64[2m]
  * each (any may be NULL to skip):

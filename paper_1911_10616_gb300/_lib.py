@@ -24,7 +24,8 @@ _ERRORS = {
 }
 
 # exported symbols of include/evoke.h
-SYMBOLS = ("evoke_count_orbits", "evoke_build_dag", "evoke_edge_orbits", "evoke_orbit_matrix",
+SYMBOLS = ("evoke_count_orbits", "evoke_build_dag", "evoke_build_dag_noalloc",
+           "evoke_edge_orbits", "evoke_orbit_matrix",
            "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
            "evoke_launch_count", "evoke_strerror", "evoke_version")
 
@@ -66,6 +67,8 @@ def load(build_if_missing: bool = True):
         lib.evoke_count_orbits.restype = ctypes.c_int
         lib.evoke_build_dag.argtypes = [vp, vp, u32, u64, vp, vp, vp]
         lib.evoke_build_dag.restype = ctypes.c_int
+        lib.evoke_build_dag_noalloc.argtypes = [vp, vp, u32, u64, vp, vp, vp]
+        lib.evoke_build_dag_noalloc.restype = ctypes.c_int
         lib.evoke_edge_orbits.argtypes = [vp, vp, u32, u64, vp, vp, vp, vp, vp, vp]
         lib.evoke_edge_orbits.restype = ctypes.c_int
         lib.evoke_orbit_matrix.argtypes = [ctypes.POINTER(ctypes.c_int64)]
@@ -162,6 +165,16 @@ def build_dag(rowptr, colidx, n: int, m: int, stream=None):
                                 _stream_handle(stream))
     _check(rc, "evoke_build_dag")
     return dp, dc[:m]
+
+
+def build_dag_noalloc(rowptr, colidx, n: int, m: int, dag_rowptr, dag_colidx, stream=None):
+    """evoke_build_dag_noalloc: fills the caller's dag_rowptr (n+1) and
+    dag_colidx (m) int32 CUDA tensors; the library allocates nothing."""
+    _check_graph(rowptr, colidx, n)
+    rc = load().evoke_build_dag_noalloc(_ptr(rowptr), _ptr(colidx), n, m, _ptr(dag_rowptr),
+                                        _ptr(dag_colidx), _stream_handle(stream))
+    _check(rc, "evoke_build_dag_noalloc")
+    return dag_rowptr, dag_colidx
 
 
 def orbit_matrix() -> np.ndarray:
