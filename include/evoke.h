@@ -72,6 +72,70 @@ int evoke_count_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t 
                        int64_t* out, const evoke_opts* opts, void* stream);
 
 /*
+ * evoke_count_batch -- induced orbit counts of every vertex of G graphs at
+ * once (many small graphs of uneven sizes).  All arrays are DEVICE memory:
+ *   rowptr_cat : uint32, the graphs' own rowptr arrays back to back; graph g
+ *                occupies entries vtx_off[g] + g .. vtx_off[g+1] + g
+ *                (n_g + 1 entries, local offsets starting at 0).
+ *   colidx_cat : uint32[edge_off[G]], the graphs' colidx arrays back to back,
+ *                local vertex ids (0 .. n_g-1).
+ *   vtx_off    : int64[G+1], prefix sums of n_g;  edge_off : int64[G+1],
+ *                prefix sums of 2 m_g.
+ *   out        : int64[vtx_off[G] * 73]; the rows of graph g start at row
+ *                vtx_off[g].  Every graph must itself be simple (see above).
+ * The graphs are processed as one disjoint union (counts of connected
+ * patterns are per component); the per-root maps are sized by the largest
+ * graph.  Limits: vtx_off[G] and edge_off[G] below 2^32 - 1.  Synchronises
+ * `stream`.  Errors as evoke_count_orbits.
+ */
+int evoke_count_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_cat,
+                      const int64_t* vtx_off, const int64_t* edge_off, uint32_t G, int64_t* out,
+                      const evoke_opts* opts, void* stream);
+
+/*
+ * Plans: the same computation split into a sizing step and a replayable
+ * execution.  evoke_plan_create / evoke_plan_create_batch take the inputs of
+ * evoke_count_orbits / evoke_count_batch (which must stay unchanged and
+ * alive while the plan is used), run the sizing passes, allocate every
+ * device buffer the execution needs (stream-ordered, on `stream`) and
+ * synchronise `stream`.  evoke_plan_execute enqueues the whole pass sequence
+ * (CSR to counts) on `stream` without any host synchronisation, so it may be
+ * captured into a CUDA graph; evoke_plan_launch_graph captures one execution
+ * into a CUDA graph on first use (and again whenever `out` changes) and
+ * launches that graph.  evoke_plan_destroy synchronises and frees.  A plan
+ * must not be executed concurrently on two streams.
+ */
+typedef struct evoke_plan evoke_plan;
+
+typedef struct evoke_plan_stats {
+  uint32_t n;                 /* vertices (all graphs of a batch) */
+  uint64_t m;                 /* undirected edges */
+  uint64_t triangles;
+  uint32_t max_degree;
+  uint32_t max_out_degree;    /* in the degree-ordered DAG */
+  uint32_t max_component;     /* largest graph of a batch; n otherwise */
+  uint64_t device_bytes;      /* device memory held by the plan */
+  int32_t kernels_per_execution;
+  int32_t root_threads;       /* threads per CTA of the per-root pass */
+  int32_t root_ctas;          /* persistent CTAs of the per-root pass */
+  int32_t root_ctas_max;      /* most CTAs evoke_plan_set_tuning accepts */
+  int32_t link_warps;
+} evoke_plan_stats;
+
+int evoke_plan_create(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                      const evoke_opts* opts, void* stream, evoke_plan** plan);
+int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_cat,
+                            const int64_t* vtx_off, const int64_t* edge_off, uint32_t G,
+                            const evoke_opts* opts, void* stream, evoke_plan** plan);
+int evoke_plan_execute(evoke_plan* plan, int64_t* out, void* stream);
+int evoke_plan_launch_graph(evoke_plan* plan, int64_t* out, void* stream);
+int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* stats);
+/* Autotuning hook: threads per CTA (256 or 512) and the number of persistent
+ * CTAs of the per-root pass, at most the number the plan was created with. */
+int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_ctas);
+int evoke_plan_destroy(evoke_plan* plan);
+
+/*
  * evoke_build_dag -- the degree-ordered DAG of Sec. 2: edge u -> v iff
  * d(u) < d(v), or d(u) = d(v) and u < v.
  *   dag_rowptr : device uint32[n+1] (written), dag_colidx : device

@@ -24,8 +24,11 @@ _ERRORS = {
 }
 
 # exported symbols of include/evoke.h
-SYMBOLS = ("evoke_count_orbits", "evoke_build_dag", "evoke_build_dag_noalloc",
-           "evoke_edge_orbits", "evoke_orbit_matrix",
+SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
+           "evoke_build_dag_noalloc", "evoke_edge_orbits", "evoke_orbit_matrix",
+           "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
+           "evoke_plan_launch_graph", "evoke_plan_info", "evoke_plan_set_tuning",
+           "evoke_plan_destroy",
            "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
            "evoke_launch_count", "evoke_strerror", "evoke_version")
 
@@ -39,6 +42,15 @@ class EvokeError(RuntimeError):
 class PhaseTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32),
                 ("calls", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("m", ctypes.c_uint64), ("triangles", ctypes.c_uint64),
+                ("max_degree", ctypes.c_uint32), ("max_out_degree", ctypes.c_uint32),
+                ("max_component", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+                ("kernels_per_execution", ctypes.c_int32), ("root_threads", ctypes.c_int32),
+                ("root_ctas", ctypes.c_int32), ("root_ctas_max", ctypes.c_int32),
+                ("link_warps", ctypes.c_int32)]
 
 
 class EvokeOpts(ctypes.Structure):
@@ -76,6 +88,19 @@ def load(build_if_missing: bool = True):
         lib.evoke_strerror.argtypes = [ctypes.c_int]
         lib.evoke_strerror.restype = ctypes.c_char_p
         lib.evoke_version.restype = ctypes.c_int
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.evoke_count_batch.argtypes = [vp, vp, vp, vp, u32, vp, ctypes.POINTER(EvokeOpts), vp]
+        lib.evoke_count_batch.restype = ctypes.c_int
+        lib.evoke_plan_create.argtypes = [vp, vp, u32, u64, ctypes.POINTER(EvokeOpts), vp, pp]
+        lib.evoke_plan_create.restype = ctypes.c_int
+        lib.evoke_plan_create_batch.argtypes = [vp, vp, vp, vp, u32, ctypes.POINTER(EvokeOpts),
+                                                vp, pp]
+        lib.evoke_plan_create_batch.restype = ctypes.c_int
+        lib.evoke_plan_execute.argtypes = [vp, vp, vp]
+        lib.evoke_plan_launch_graph.argtypes = [vp, vp, vp]
+        lib.evoke_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
+        lib.evoke_plan_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        lib.evoke_plan_destroy.argtypes = [vp]
         lib.evoke_profile_enable.argtypes = [ctypes.c_int]
         lib.evoke_profile_read.argtypes = [ctypes.POINTER(PhaseTime), ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int)]
@@ -141,6 +166,100 @@ def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = Fals
                                    ctypes.byref(opts), _stream_handle(stream))
     _check(rc, "evoke_count_orbits")
     return out
+
+
+def batch_to_device(graphs, device="cuda"):
+    """Concatenate graphgen.Graph objects for evoke_count_batch: returns
+    (rowptr_cat, colidx_cat, vtx_off, edge_off) CUDA tensors."""
+    import torch
+    from . import graphgen
+    rp, col, vo, eo = graphgen.concat_batch(graphs)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    return (t(rp.astype(np.uint32).view(np.int32)), t(col.astype(np.uint32).view(np.int32)),
+            t(vo.astype(np.int64)), t(eo.astype(np.int64)))
+
+
+def count_batch(rowptr_cat, colidx_cat, vtx_off, edge_off, out=None, validate: bool = False,
+                stream=None):
+    """Induced orbit counts of a batch of graphs, int64 [sum n_g, 73]."""
+    import torch
+    G = vtx_off.numel() - 1
+    N = int(vtx_off[-1].item())
+    if out is None:
+        out = torch.empty((N, NORB), dtype=torch.int64, device=vtx_off.device)
+    opts = EvokeOpts(1 if validate else 0, 0, 0, 0)
+    rc = load().evoke_count_batch(_ptr(rowptr_cat), _ptr(colidx_cat), _ptr(vtx_off),
+                                  _ptr(edge_off), G, _ptr(out), ctypes.byref(opts),
+                                  _stream_handle(stream))
+    _check(rc, "evoke_count_batch")
+    return out
+
+
+class Plan:
+    """A sized, allocated execution plan (evoke_plan_*).  Keep the input
+    tensors alive and unchanged while the plan exists."""
+
+    def __init__(self, handle, inputs, n):
+        self._h = handle
+        self._inputs = inputs
+        self.n = n
+
+    @classmethod
+    def single(cls, rowptr, colidx, n: int, m: int, validate: bool = False, stream=None):
+        _check_graph(rowptr, colidx, n)
+        h = ctypes.c_void_p()
+        opts = EvokeOpts(1 if validate else 0, 0, 0, 0)
+        _check(load().evoke_plan_create(_ptr(rowptr), _ptr(colidx), n, m, ctypes.byref(opts),
+                                        _stream_handle(stream), ctypes.byref(h)),
+               "evoke_plan_create")
+        return cls(h, (rowptr, colidx), n)
+
+    @classmethod
+    def batch(cls, rowptr_cat, colidx_cat, vtx_off, edge_off, validate: bool = False,
+              stream=None):
+        h = ctypes.c_void_p()
+        opts = EvokeOpts(1 if validate else 0, 0, 0, 0)
+        G = vtx_off.numel() - 1
+        _check(load().evoke_plan_create_batch(_ptr(rowptr_cat), _ptr(colidx_cat), _ptr(vtx_off),
+                                              _ptr(edge_off), G, ctypes.byref(opts),
+                                              _stream_handle(stream), ctypes.byref(h)),
+               "evoke_plan_create_batch")
+        return cls(h, (rowptr_cat, colidx_cat, vtx_off, edge_off), int(vtx_off[-1].item()))
+
+    def new_output(self):
+        import torch
+        dev = self._inputs[0].device
+        return torch.empty((self.n, NORB), dtype=torch.int64, device=dev)
+
+    def execute(self, out, stream=None):
+        _check(load().evoke_plan_execute(self._h, _ptr(out), _stream_handle(stream)),
+               "evoke_plan_execute")
+        return out
+
+    def launch_graph(self, out, stream=None):
+        _check(load().evoke_plan_launch_graph(self._h, _ptr(out), _stream_handle(stream)),
+               "evoke_plan_launch_graph")
+        return out
+
+    def info(self) -> dict:
+        st = PlanStats()
+        _check(load().evoke_plan_info(self._h, ctypes.byref(st)), "evoke_plan_info")
+        return {f: getattr(st, f) for f, _ in PlanStats._fields_}
+
+    def set_tuning(self, root_threads: int, root_ctas: int):
+        _check(load().evoke_plan_set_tuning(self._h, int(root_threads), int(root_ctas)),
+               "evoke_plan_set_tuning")
+
+    def destroy(self):
+        if self._h:
+            load().evoke_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def edge_orbits(rowptr, colidx, n: int, m: int, stream=None):

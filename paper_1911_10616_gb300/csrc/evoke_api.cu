@@ -312,25 +312,74 @@ __global__ void copy_i64_kernel(const u64* in, long long* out, u64 count) {
   if (i < count) out[i] = (long long)in[i];
 }
 
-// Everything that the passes need, laid out in device memory.
-struct Run {
+// ---------------------------------------------------------------------------
+// Plans.  A plan owns every device buffer the pass sequence needs for one
+// input (one graph, or one batch of graphs as their disjoint union).  Creating
+// it runs the sizing passes (DAG, triangle counts) and synchronises the
+// stream; executing it enqueues the whole pass sequence, from the CSR to the
+// int64[n x 73] counts, with no host synchronisation (so it can be captured
+// into a CUDA graph and replayed).
+// ---------------------------------------------------------------------------
+struct Config {
+  int root_threads = 512;
+  int root_ctas = 0;      // 0: 2 per SM (512 threads) / 4 per SM (256)
+  u32 link_warps = 0;     // 0: 64 per SM
+};
+
+}  // namespace
+
+struct evoke_plan {
+  // input
+  const u32* rowptr = nullptr;
+  const u32* col = nullptr;
+  u32 n = 0;
+  u64 m = 0;
+  // batch input (the union CSR below is rebuilt from it on every execution)
+  bool batch = false;
+  const u32* rowptr_cat = nullptr;
+  const u32* col_cat = nullptr;
+  const long long* vtx_off = nullptr;
+  const long long* edge_off = nullptr;
+  u32 G = 0;
+  u32 max_comp = 0;
+  // sizes
+  u32 dmax = 0, max_outdeg = 0;
+  u64 ntri_entries = 0;
+  Config cfg;
+  K5Config k5{};
+  // device memory
+  void* block = nullptr;
+  size_t bytes = 0;
+  void* block2 = nullptr;
+  size_t bytes2 = 0;
   Graph g{};
   SlotArrays sa{};
   u64* acc = nullptr;
-  int* status = nullptr;
-  u32* misc = nullptr;  // [0] dmax
+  RootScratch rs{};
+  u32* pref = nullptr;
+  u32 pref_stride = 0;
+  u32* link_scratch = nullptr;
   u32* cnt = nullptr;
   void* scan_tmp = nullptr;
-  void* block = nullptr;
-  void* block2 = nullptr;
+  int* status = nullptr;
+  u32* misc = nullptr;
+  u32* union_rowptr = nullptr;
+  u32* union_col = nullptr;
+  u32* comp_base = nullptr;
   cudaStream_t st = nullptr;
-  u32 dmax = 0;
-  u32 max_outdeg = 0;
-  u64 ntri_entries = 0;
+  int launches_per_exec = 0;
+  int ctas_alloc = 0;     // CTAs the root maps were allocated for
+  // CUDA graph of one execution
+  cudaGraphExec_t gexec = nullptr;
+  long long* gexec_out = nullptr;
 };
 
-int check_args(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-               cudaStream_t st) {
+namespace {
+
+int sm_count_cached() { return sm_count(); }
+
+int check_csr(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+              cudaStream_t st) {
   if (n == 0xffffffffu || 2 * m >= 0xffffffffull) return EVOKE_ERANGE;
   if (!rowptr) return EVOKE_EINVAL;
   if (m > 0 && !colidx) return EVOKE_EINVAL;
@@ -343,79 +392,257 @@ int check_args(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint6
   return EVOKE_OK;
 }
 
-// Stages shared by every entry point: degrees, validation, reverse slots,
-// DAG, triangle counts and lists.
-int prepare(Run& R, const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-            bool validate, bool need_lists, cudaStream_t st) {
-  R.st = st;
-  const u64 S = 2 * m;
+void apply_config(evoke_plan* P, u32 map_n) {
+  const int sms = sm_count_cached();
+  P->rs.threads = P->cfg.root_threads == 256 ? 256 : 512;
+  P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (P->rs.threads == 256 ? 4 : 2);
+  // maps for up to 4 CTAs per SM when that is cheap, so that tuning can
+  // raise the CTA count later
+  const size_t per_cta = (size_t)map_n * (sizeof(MapRec) + 2 * sizeof(u32));
+  P->ctas_alloc = P->rs.ctas;
+  if ((size_t)sms * 4 * per_cta <= ((size_t)4 << 30)) P->ctas_alloc = std::max(P->ctas_alloc, sms * 4);
+}
+
+// stage 1 buffers (graph-sized) and the sizing passes
+int plan_stage1(evoke_plan* P, bool validate) {
+  cudaStream_t st = P->st;
+  const u32 n = P->n;
+  const u64 m = P->m, S = 2 * m;
   size_t bytes = sz<u32>(n) + sz<u32>(S) + sz<u32>(n + 1) + 2 * sz<u32>(m) + sz<u32>(n) +
                  sz<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1)) + sz<u32>(S) +
                  sz<u64>(S + 1) + sz<int>(4) + sz<u32>(4);
-  if (cudaMallocAsync(&R.block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
-  Arena ar{static_cast<char*>(R.block), bytes, 0, st};
-  Graph& g = R.g;
+  if (P->batch) bytes += sz<u32>(n + 1) + sz<u32>(S) + sz<u32>(n);
+  if (cudaMallocAsync(&P->block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  P->bytes = bytes;
+  Arena ar{static_cast<char*>(P->block), bytes, 0, st};
+  Graph& g = P->g;
+  if (P->batch) {
+    P->union_rowptr = ar.take<u32>(n + 1);
+    P->union_col = ar.take<u32>(S);
+    P->comp_base = ar.take<u32>(n);
+    P->rowptr = P->union_rowptr;
+    P->col = P->union_col;
+  }
   g.n = n;
   g.S = S;
-  g.rowptr = rowptr;
-  g.col = colidx;
+  g.rowptr = P->rowptr;
+  g.col = P->col;
   g.deg = ar.take<u32>(n);
   g.rev = ar.take<u32>(S);
   g.dag_ptr = ar.take<u32>(n + 1);
   g.dag_col = ar.take<u32>(m);
   g.dag_slot = ar.take<u32>(m);
-  R.cnt = ar.take<u32>(n);
-  R.scan_tmp = ar.take<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1));
-  R.sa.T = ar.take<u32>(S);
+  P->cnt = ar.take<u32>(n);
+  P->scan_tmp = ar.take<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1));
+  P->sa.T = ar.take<u32>(S);
   g.tl_ptr = ar.take<u64>(S + 1);
-  R.status = ar.take<int>(4);
-  R.misc = ar.take<u32>(4);
+  P->status = ar.take<int>(4);
+  P->misc = ar.take<u32>(4);
   if (ar.overflow) return EVOKE_ENOMEM;
-  cudaMemsetAsync(R.status, 0, sizeof(int) * 4, st);
-  cudaMemsetAsync(R.misc, 0, sizeof(u32) * 4, st);
-  phase("degrees", n ? 1 : 0, st, [&] { launch_degrees(g, st); });
-  phase("rev_validate", n ? 1 : 0, st, [&] { launch_rev_validate(g, R.status, st); });
+  cudaMemsetAsync(P->status, 0, sizeof(int) * 4, st);
+  cudaMemsetAsync(P->misc, 0, sizeof(u32) * 4, st);
+  if (P->batch)
+    launch_union_csr(P->rowptr_cat, P->col_cat, P->vtx_off, P->edge_off, P->G, n, S,
+                     P->union_rowptr, P->union_col, P->comp_base, st);
+  launch_degrees(g, st);
+  launch_rev_validate(g, P->status, st);
   if (validate) {
     int status = 0;
-    cudaMemcpyAsync(&status, R.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&status, P->status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
     if (status & ST_RANGE) return EVOKE_ERANGE;
     if (status & ST_NOT_SIMPLE) return EVOKE_ENOTSIMPLE;
   }
-  phase("dag", n ? 5 : 0, st, [&] { launch_dag(g, R.cnt, R.scan_tmp, st); });
-  phase("dmax", n ? 1 : 0, st, [&] {
-    if (n) dmax_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.deg, g.dag_ptr, n, R.misc);
-  });
-  if (!need_lists) return EVOKE_OK;
-  phase("tri_count", m ? 1 : 0, st, [&] { launch_tri_count(g, R.sa.T, st); });
-  phase("tri_scan", S ? 3 : 0, st, [&] { launch_scan_u32_to_u64(R.sa.T, g.tl_ptr, S, R.scan_tmp, st); });
+  launch_dag(g, P->cnt, P->scan_tmp, st);
+  if (n) dmax_kernel<<<(n + 255) / 256, 256, 0, st>>>(g.deg, g.dag_ptr, n, P->misc);
+  launch_tri_count(g, P->sa.T, st);
+  launch_scan_u32_to_u64(P->sa.T, g.tl_ptr, S, P->scan_tmp, st);
   u64 total = 0;
   u32 mx[2] = {0, 0};
   cudaMemcpyAsync(&total, g.tl_ptr + S, sizeof(u64), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(mx, R.misc, 2 * sizeof(u32), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(mx, P->misc, 2 * sizeof(u32), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
-  R.ntri_entries = total;
-  R.dmax = mx[0];
-  R.max_outdeg = mx[1];
-  if (cudaMallocAsync(&R.block2, sz<u32>(total), st) != cudaSuccess) return EVOKE_ENOMEM;
-  g.tl = static_cast<u32*>(R.block2);
-  phase("tri_fill", m ? 1 : 0, st, [&] { launch_tri_fill(g, R.sa.T, st); });
+  P->ntri_entries = total;
+  P->dmax = mx[0];
+  P->max_outdeg = mx[1];
   return EVOKE_OK;
 }
 
-void release(Run& R) {
-  if (R.block) cudaFreeAsync(R.block, R.st);
-  if (R.block2) cudaFreeAsync(R.block2, R.st);
-  R.block = R.block2 = nullptr;
+// stage 2 buffers: triangle lists, per-slot arrays, accumulators, scratch
+int plan_stage2(evoke_plan* P) {
+  cudaStream_t st = P->st;
+  const u32 n = P->n;
+  const u64 S = P->g.S;
+  const u32 map_n = P->batch ? std::max<u32>(P->max_comp, 1) : std::max<u32>(n, 1);
+  apply_config(P, map_n);
+  const int ctas = P->ctas_alloc;
+  const u32 dmax = std::max<u32>(P->dmax, 1);
+  P->cfg.link_warps = P->cfg.link_warps ? P->cfg.link_warps : (u32)sm_count_cached() * 64;
+  P->cfg.link_warps = (P->cfg.link_warps + 7) / 8 * 8;
+  const u32 link_warps = P->cfg.link_warps;
+  P->pref_stride = dmax + 1;
+  const bool root_profile = [] {
+    const char* e = getenv("EVOKE_ROOT_PROFILE");
+    return e && *e && *e != '0';
+  }();
+  size_t bytes = sz<u32>(P->ntri_entries) + 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) +
+                 sz<u64>((size_t)NACC * n) + root_scratch_bytes(map_n, ctas) + 256 * 8 +
+                 sz<u32>(n) + sz<u32>(64) + sz<u32>(4) +
+                 sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * dmax);
+  if (cudaMallocAsync(&P->block2, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  P->bytes2 = bytes;
+  Arena ar{static_cast<char*>(P->block2), bytes, 0, st};
+  P->g.tl = ar.take<u32>(P->ntri_entries);
+  SlotArrays& sa = P->sa;
+  sa.E5 = ar.take<u64>(S);
+  sa.E7 = ar.take<u64>(S);
+  sa.E9 = ar.take<u64>(S);
+  sa.K4 = ar.take<u64>(S);
+  sa.b49 = ar.take<u64>(S);
+  sa.b62 = ar.take<u64>(S);
+  sa.b64 = ar.take<u64>(S);
+  sa.b68 = ar.take<u64>(S);
+  sa.bc5 = ar.take<u64>(S);
+  sa.Mmid = ar.take<u32>(S);
+  sa.Mtop = ar.take<u32>(S);
+  P->acc = ar.take<u64>((size_t)NACC * n);
+  RootScratch& rs = P->rs;
+  rs.map_n = map_n;
+  rs.comp_base = P->batch ? P->comp_base : nullptr;
+  rs.map = ar.take<MapRec>((size_t)ctas * map_n);
+  rs.touched = ar.take<u32>((size_t)ctas * map_n);
+  rs.jlist = ar.take<u32>((size_t)ctas * map_n);
+  rs.order = ar.take<u32>(n);
+  rs.bucket_cnt = ar.take<u32>(64);
+  rs.head = ar.take<u32>(4);
+  rs.tsrc = P->acc + (size_t)A_TSRC * n;
+  rs.prof = root_profile ? ar.take<u64>(8) : nullptr;
+  rs.cycles = nullptr;
+  P->pref = ar.take<u32>((size_t)ctas * P->pref_stride);
+  P->link_scratch = ar.take<u32>((size_t)link_warps * dmax);
+  if (ar.overflow) return EVOKE_ENOMEM;
+  // maps and scratch rows are left zeroed by the kernels that use them
+  cudaMemsetAsync(P->block2, 0, ar.used, st);
+  P->k5 = k5_configure(P->max_outdeg);
+  return EVOKE_OK;
 }
 
-int finish(Run& R, int rc) {
+// zero what is accumulated into during one execution
+void clear_accumulators(evoke_plan* P, cudaStream_t st) {
+  const u64 S = P->g.S;
+  const size_t slot_bytes = (char*)(P->sa.Mmid) - (char*)(P->sa.E5);  // E5 .. bc5 contiguous
+  cudaMemsetAsync(P->sa.E5, 0, slot_bytes, st);
+  cudaMemsetAsync(P->acc, 0, sizeof(u64) * (size_t)NACC * P->n, st);
+  if (P->rs.prof) cudaMemsetAsync(P->rs.prof, 0, sizeof(u64) * 8, st);
+  (void)S;
+}
+
+// the whole pass sequence; no host synchronisation
+void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
+  Graph& g = P->g;
+  SlotArrays& sa = P->sa;
+  u64* acc = P->acc;
+  const u32 n = P->n;
+  const u64 S = g.S;
+  const int nl = n ? 1 : 0, sl = S ? 1 : 0;
+  auto run = [&](const char* name, int launches, auto&& fn) {
+    if (timed) phase(name, launches, st, fn);
+    else fn();
+  };
+  run("memset", 0, [&] { clear_accumulators(P, st); });
+  if (P->batch)
+    run("union_csr", 1 + sl, [&] {
+      launch_union_csr(P->rowptr_cat, P->col_cat, P->vtx_off, P->edge_off, P->G, n, S,
+                       P->union_rowptr, P->union_col, P->comp_base, st);
+    });
+  run("degrees", nl, [&] { launch_degrees(g, st); });
+  run("rev", nl, [&] { launch_rev_validate(g, P->status, st); });
+  run("dag", n ? 5 : 0, [&] { launch_dag(g, P->cnt, P->scan_tmp, st); });
+  run("tri_count", sl, [&] { launch_tri_count(g, sa.T, st); });
+  run("tri_scan", S ? 3 : 0, [&] { launch_scan_u32_to_u64(sa.T, g.tl_ptr, S, P->scan_tmp, st); });
+  run("tri_fill", sl, [&] { launch_tri_fill(g, sa.T, st); });
+  run("tri_edge", sl, [&] { launch_tri_edge(g, sa, st); });
+  run("vsum1", nl, [&] { launch_vsum1(g, sa, acc, st); });
+  run("tri_opp1", nl, [&] { launch_tri_opp1(g, sa, acc, st); });
+  run("k4", (P->ntri_entries ? 1 : 0) + sl, [&] { launch_k4_known(g, sa, acc, P->ntri_entries, st); });
+  run("schedule", 3 * nl, [&] { launch_schedule(g, acc, P->rs, st); });
+  run("root", nl, [&] { launch_root_with_pref(g, sa, acc, P->rs, P->pref, P->pref_stride, st); });
+  run("link", sl, [&] {
+    launch_link(g, sa, P->link_scratch, P->cfg.link_warps, std::max<u32>(P->dmax, 1), st);
+  });
+  run("k5", P->k5.blocks ? 1 : 0, [&] { launch_k5(g, acc, P->k5, st); });
+  run("tri_opp2", nl, [&] { launch_tri_opp2(g, sa, acc, st); });
+  run("vsum2", nl, [&] { launch_vsum2(g, sa, acc, st); });
+  run("vsum3", nl, [&] { launch_vsum3(g, acc, st); });
+  if (out) run("finalize", nl, [&] { launch_finalize(g, acc, out, st); });
+}
+
+int count_launches(const evoke_plan* P, bool with_out) {
+  const int nl = P->n ? 1 : 0, sl = P->g.S ? 1 : 0;
+  int k = 0;
+  if (P->batch) k += 1 + sl;
+  k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + sl + nl + nl;
+  k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl + sl + (P->k5.blocks ? 1 : 0) + nl + nl + nl;
+  if (with_out) k += nl;
+  return k;
+}
+
+void plan_free(evoke_plan* P) {
+  if (!P) return;
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->block) cudaFreeAsync(P->block, P->st);
+  if (P->block2) cudaFreeAsync(P->block2, P->st);
+  cudaStreamSynchronize(P->st);
+  delete P;
+}
+
+int plan_finish_create(evoke_plan* P, evoke_plan** out_plan) {
   cudaError_t e = cudaGetLastError();
-  release(R);
-  cudaError_t e2 = cudaStreamSynchronize(R.st);
-  if (rc != EVOKE_OK) return rc;
-  if (e != cudaSuccess || e2 != cudaSuccess) return EVOKE_ECUDA;
+  if (e != cudaSuccess) {
+    plan_free(P);
+    return EVOKE_ECUDA;
+  }
+  *out_plan = P;
   return EVOKE_OK;
+}
+
+int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                  const evoke_opts* opts, cudaStream_t st, evoke_plan** out_plan) {
+  int rc = ensure_transform();
+  if (rc) return rc;
+  rc = check_csr(rowptr, colidx, n, m, st);
+  if (rc) return rc;
+  evoke_plan* P = new evoke_plan();
+  P->rowptr = rowptr;
+  P->col = colidx;
+  P->n = n;
+  P->m = m;
+  P->st = st;
+  if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
+  rc = plan_stage1(P, opts && opts->validate);
+  if (!rc) rc = plan_stage2(P);
+  if (rc) {
+    plan_free(P);
+    return rc;
+  }
+  P->launches_per_exec = count_launches(P, true);
+  return plan_finish_create(P, out_plan);
+}
+
+// synchronous one-shot run on a plan, with the phase profiler
+int run_once(evoke_plan* P, long long* out, cudaStream_t st) {
+  execute(P, out, st, /*timed=*/true);  // phase() counts the launches
+  if (P->rs.prof) {
+    u64 pc[8] = {};
+    cudaMemcpyAsync(pc, P->rs.prof, sizeof(pc), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    fprintf(stderr, "evoke root phases (Gcycles summed over CTAs): wedges %.2f, diamonds+R %.2f, "
+                    "3-path push %.2f, wedges2+k %.2f, scan %.2f\n",
+            pc[0] * 1e-9, pc[1] * 1e-9, pc[2] * 1e-9, pc[3] * 1e-9, pc[4] * 1e-9);
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? EVOKE_OK : EVOKE_ECUDA;
 }
 
 }  // namespace
@@ -480,145 +707,243 @@ int evoke_orbit_matrix(int64_t* A) {
   return EVOKE_OK;
 }
 
-int evoke_build_dag(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-                    uint32_t* dag_rowptr, uint32_t* dag_colidx, void* stream) {
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!dag_rowptr || (m && !dag_colidx)) return EVOKE_EINVAL;
-  int rc = check_args(rowptr, colidx, n, m, st);
-  if (rc) return rc;
-  Run R;
-  rc = prepare(R, rowptr, colidx, n, m, false, false, st);
-  if (rc == EVOKE_OK) {
-    cudaMemcpyAsync(dag_rowptr, R.g.dag_ptr, sizeof(u32) * (n + 1), cudaMemcpyDeviceToDevice, st);
-    if (m)
-      cudaMemcpyAsync(dag_colidx, R.g.dag_col, sizeof(u32) * m, cudaMemcpyDeviceToDevice, st);
-  }
-  return finish(R, rc);
+
+int evoke_plan_create(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                      const evoke_opts* opts, void* stream, evoke_plan** plan) {
+  if (!plan) return EVOKE_EINVAL;
+  *plan = nullptr;
+  return create_single(rowptr, colidx, n, m, opts, static_cast<cudaStream_t>(stream), plan);
 }
 
-int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-                      int64_t* tri, int64_t* c4, int64_t* k4, int64_t* e7, int64_t* e9,
-                      void* stream);
-
-int evoke_count_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-                       int64_t* out, const evoke_opts* opts, void* stream);
-
-}  // extern "C"
-
-namespace {
-
-// The full pass sequence.  `out` may be null (intermediates only).
-int run_all(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-            int64_t* out, const evoke_opts* opts, cudaStream_t st, int64_t* e_tri,
-            int64_t* e_c4, int64_t* e_k4, int64_t* e_e7, int64_t* e_e9) {
+int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_cat,
+                            const int64_t* vtx_off, const int64_t* edge_off, uint32_t G,
+                            const evoke_opts* opts, void* stream, evoke_plan** plan) {
+  if (!plan || !rowptr_cat || !vtx_off || !edge_off) return EVOKE_EINVAL;
+  *plan = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = ensure_transform();
   if (rc) return rc;
-  rc = check_args(rowptr, colidx, n, m, st);
-  if (rc) return rc;
-  if (n && out == nullptr && !e_tri && !e_c4 && !e_k4 && !e_e7 && !e_e9) return EVOKE_EINVAL;
-  Run R;
-  rc = prepare(R, rowptr, colidx, n, m, opts && opts->validate, true, st);
-  if (rc) return finish(R, rc);
-  Graph& g = R.g;
-  const u64 S = g.S;
-  const int ctas = (opts && opts->root_ctas > 0) ? opts->root_ctas : 2 * sm_count();
-  const u32 dmax = std::max<u32>(R.dmax, 1);
-  const u32 link_warps = (u32)sm_count() * 64;  // multiple of 8
-  const u32 pref_stride = dmax + 1;
-  // second arena: slot arrays, accumulators, scratch
-  const bool root_profile = [] {
-    const char* e = getenv("EVOKE_ROOT_PROFILE");
-    return e && *e && *e != '0';
-  }();
-  size_t bytes = 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) + sz<u64>((size_t)NACC * n) +
-                 root_scratch_bytes(n, ctas) + 256 * 8 + sz<u32>(n) + sz<u32>(64) + sz<u32>(4) +
-                 sz<u32>((size_t)ctas * pref_stride) + sz<u32>((size_t)link_warps * dmax);
-  void* blk = nullptr;
-  if (cudaMallocAsync(&blk, bytes, st) != cudaSuccess) return finish(R, EVOKE_ENOMEM);
-  Arena ar{static_cast<char*>(blk), bytes, 0, st};
-  SlotArrays& sa = R.sa;
-  sa.E5 = ar.take<u64>(S);
-  sa.E7 = ar.take<u64>(S);
-  sa.E9 = ar.take<u64>(S);
-  sa.K4 = ar.take<u64>(S);
-  sa.b49 = ar.take<u64>(S);
-  sa.b62 = ar.take<u64>(S);
-  sa.b64 = ar.take<u64>(S);
-  sa.b68 = ar.take<u64>(S);
-  sa.bc5 = ar.take<u64>(S);
-  u64* acc = ar.take<u64>((size_t)NACC * n);
-  RootScratch rs{};
-  rs.ctas = ctas;
-  rs.map = ar.take<MapRec>((size_t)ctas * n);
-  rs.touched = ar.take<u32>((size_t)ctas * n);
-  rs.jlist = ar.take<u32>((size_t)ctas * n);
-  rs.order = ar.take<u32>(n);
-  rs.bucket_cnt = ar.take<u32>(64);
-  rs.head = ar.take<u32>(4);
-  rs.tsrc = acc + (size_t)A_TSRC * n;
-  rs.prof = root_profile ? ar.take<u64>(8) : nullptr;
-  rs.cycles = nullptr;
-  sa.Mmid = ar.take<u32>(S);
-  sa.Mtop = ar.take<u32>(S);
-  u32* pref = ar.take<u32>((size_t)ctas * pref_stride);
-  u32* link_scratch = ar.take<u32>((size_t)link_warps * dmax);
-  if (ar.overflow) {
-    cudaFreeAsync(blk, st);
-    return finish(R, EVOKE_ENOMEM);
+  long long tot[2] = {0, 0};
+  if (cudaMemcpyAsync(&tot[0], vtx_off + G, sizeof(long long), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&tot[1], edge_off + G, sizeof(long long), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess)
+    return EVOKE_EINVAL;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
+  if (tot[0] < 0 || tot[1] < 0 || (tot[1] & 1)) return EVOKE_EINVAL;
+  if (tot[0] >= 0xffffffffll || tot[1] >= 0xffffffffll) return EVOKE_ERANGE;
+  if (tot[1] && !colidx_cat) return EVOKE_EINVAL;
+  evoke_plan* P = new evoke_plan();
+  P->batch = true;
+  P->rowptr_cat = rowptr_cat;
+  P->col_cat = colidx_cat;
+  P->vtx_off = reinterpret_cast<const long long*>(vtx_off);
+  P->edge_off = reinterpret_cast<const long long*>(edge_off);
+  P->G = G;
+  P->n = (u32)tot[0];
+  P->m = (u64)tot[1] / 2;
+  P->st = st;
+  if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
+  // the largest component sizes the per-CTA maps of the root pass
+  {
+    u32* d = nullptr;
+    if (cudaMallocAsync(&d, sizeof(u32), st) != cudaSuccess) {
+      delete P;
+      return EVOKE_ENOMEM;
+    }
+    cudaMemsetAsync(d, 0, sizeof(u32), st);
+    launch_max_component(P->vtx_off, G, d, st);
+    u32 mc = 0;
+    cudaMemcpyAsync(&mc, d, sizeof(u32), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      delete P;
+      return EVOKE_ECUDA;
+    }
+    P->max_comp = mc;
   }
-  // zero everything that is accumulated into
-  cudaMemsetAsync(blk, 0, ar.used, st);
-
-  const int nl = n ? 1 : 0, sl = S ? 1 : 0;
-  phase("tri_edge", sl, st, [&] { launch_tri_edge(g, sa, st); });
-  phase("vsum1", nl, st, [&] { launch_vsum1(g, sa, acc, st); });
-  phase("tri_opp1", nl, st, [&] { launch_tri_opp1(g, sa, acc, st); });
-  phase("k4", (R.ntri_entries ? 1 : 0) + sl, st, [&] { launch_k4(g, sa, acc, st); });
-  phase("schedule", 3 * nl, st, [&] { launch_schedule(g, acc, rs, st); });
-  phase("root", nl, st, [&] { launch_root_with_pref(g, sa, acc, rs, pref, pref_stride, st); });
-  if (rs.prof) {
-    u64 pc[8] = {};
-    cudaMemcpyAsync(pc, rs.prof, sizeof(pc), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    fprintf(stderr, "evoke root phases (Gcycles summed over CTAs): wedges %.2f, diamonds+R %.2f, "
-                    "3-path push %.2f, wedges2+k %.2f, scan %.2f\n",
-            pc[0] * 1e-9, pc[1] * 1e-9, pc[2] * 1e-9, pc[3] * 1e-9, pc[4] * 1e-9);
+  rc = plan_stage1(P, opts && opts->validate);
+  if (!rc) rc = plan_stage2(P);
+  if (rc) {
+    plan_free(P);
+    return rc;
   }
-  phase("link", sl, st, [&] { launch_link(g, sa, link_scratch, link_warps, dmax, st); });
-  phase("k5", sl, st, [&] { launch_k5(g, acc, R.max_outdeg, st); });
-  phase("tri_opp2", nl, st, [&] { launch_tri_opp2(g, sa, acc, st); });
-  phase("vsum2", nl, st, [&] { launch_vsum2(g, sa, acc, st); });
-  phase("vsum3", nl, st, [&] { launch_vsum3(g, acc, st); });
-  if (out) phase("finalize", nl, st, [&] { launch_finalize(g, acc, reinterpret_cast<long long*>(out), st); });
-  const unsigned eb = (unsigned)((S + 255) / 256);
-  if (S) {
-    if (e_tri) widen_kernel<<<eb, 256, 0, st>>>(sa.T, reinterpret_cast<long long*>(e_tri), S);
-    if (e_c4) copy_i64_kernel<<<eb, 256, 0, st>>>(sa.E5, reinterpret_cast<long long*>(e_c4), S);
-    if (e_k4) copy_i64_kernel<<<eb, 256, 0, st>>>(sa.K4, reinterpret_cast<long long*>(e_k4), S);
-    if (e_e7) copy_i64_kernel<<<eb, 256, 0, st>>>(sa.E7, reinterpret_cast<long long*>(e_e7), S);
-    if (e_e9) copy_i64_kernel<<<eb, 256, 0, st>>>(sa.E9, reinterpret_cast<long long*>(e_e9), S);
-  }
-  cudaFreeAsync(blk, st);
-  return finish(R, EVOKE_OK);
+  P->launches_per_exec = count_launches(P, true);
+  return plan_finish_create(P, plan);
 }
 
-}  // namespace
+int evoke_plan_execute(evoke_plan* plan, int64_t* out, void* stream) {
+  if (!plan || (plan->n && !out)) return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches += (unsigned long long)plan->launches_per_exec;
+  }
+  execute(plan, reinterpret_cast<long long*>(out), st, /*timed=*/false);
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
 
-extern "C" {
+int evoke_plan_launch_graph(evoke_plan* plan, int64_t* out, void* stream) {
+  if (!plan || (plan->n && !out)) return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  long long* o = reinterpret_cast<long long*>(out);
+  if (!plan->gexec || plan->gexec_out != o) {
+    if (plan->gexec) {
+      cudaGraphExecDestroy(plan->gexec);
+      plan->gexec = nullptr;
+    }
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return EVOKE_ECUDA;
+    cudaGraph_t graph = nullptr;
+    int rc = EVOKE_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = EVOKE_ECUDA;
+    if (!rc) {
+      execute(plan, o, cs, /*timed=*/false);
+      if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) rc = EVOKE_ECUDA;
+    }
+    if (!rc && cudaGraphInstantiate(&plan->gexec, graph, 0) != cudaSuccess) rc = EVOKE_ECUDA;
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc) {
+      cudaGetLastError();
+      return rc;
+    }
+    plan->gexec_out = o;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches += (unsigned long long)plan->launches_per_exec;
+  }
+  return cudaGraphLaunch(plan->gexec, st) == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
+
+int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* out) {
+  if (!plan || !out) return EVOKE_EINVAL;
+  out->n = plan->n;
+  out->m = plan->m;
+  out->triangles = plan->ntri_entries / 6;
+  out->max_degree = plan->dmax;
+  out->max_out_degree = plan->max_outdeg;
+  out->max_component = plan->batch ? plan->max_comp : plan->n;
+  out->device_bytes = plan->bytes + plan->bytes2;
+  out->kernels_per_execution = plan->launches_per_exec;
+  out->root_threads = plan->rs.threads;
+  out->root_ctas = plan->rs.ctas;
+  out->root_ctas_max = plan->ctas_alloc;
+  out->link_warps = (int32_t)plan->cfg.link_warps;
+  return EVOKE_OK;
+}
+
+int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_ctas) {
+  if (!plan || (root_threads != 256 && root_threads != 512) || root_ctas <= 0) return EVOKE_EINVAL;
+  const int per_sm_max = root_threads == 256 ? 4 : 2;
+  if (root_ctas > sm_count_cached() * per_sm_max * 4) return EVOKE_ERANGE;
+  // the per-CTA maps were sized when the plan was created
+  if (root_ctas > plan->ctas_alloc) return EVOKE_ERANGE;
+  if (plan->gexec) {
+    cudaGraphExecDestroy(plan->gexec);
+    plan->gexec = nullptr;
+  }
+  plan->cfg.root_threads = root_threads;
+  plan->rs.threads = root_threads;
+  plan->rs.ctas = root_ctas;
+  return EVOKE_OK;
+}
+
+int evoke_plan_destroy(evoke_plan* plan) {
+  if (!plan) return EVOKE_EINVAL;
+  plan_free(plan);
+  return EVOKE_OK;
+}
 
 int evoke_count_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
                        int64_t* out, const evoke_opts* opts, void* stream) {
   if (n && !out) return EVOKE_EINVAL;
-  return run_all(rowptr, colidx, n, m, out, opts, static_cast<cudaStream_t>(stream), nullptr,
-                 nullptr, nullptr, nullptr, nullptr);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  evoke_plan* P = nullptr;
+  int rc = create_single(rowptr, colidx, n, m, opts, st, &P);
+  if (rc) return rc;
+  rc = run_once(P, reinterpret_cast<long long*>(out), st);
+  plan_free(P);
+  return rc;
+}
+
+int evoke_count_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_cat,
+                      const int64_t* vtx_off, const int64_t* edge_off, uint32_t G, int64_t* out,
+                      const evoke_opts* opts, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  evoke_plan* P = nullptr;
+  int rc = evoke_plan_create_batch(rowptr_cat, colidx_cat, vtx_off, edge_off, G, opts, stream, &P);
+  if (rc) return rc;
+  if (P->n && !out) {
+    plan_free(P);
+    return EVOKE_EINVAL;
+  }
+  rc = run_once(P, reinterpret_cast<long long*>(out), st);
+  plan_free(P);
+  return rc;
 }
 
 int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
                       int64_t* tri, int64_t* c4, int64_t* k4, int64_t* e7, int64_t* e9,
                       void* stream) {
   if (!tri && !c4 && !k4 && !e7 && !e9) return EVOKE_EINVAL;
-  return run_all(rowptr, colidx, n, m, nullptr, nullptr, static_cast<cudaStream_t>(stream), tri,
-                 c4, k4, e7, e9);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  evoke_plan* P = nullptr;
+  int rc = create_single(rowptr, colidx, n, m, nullptr, st, &P);
+  if (rc) return rc;
+  rc = run_once(P, nullptr, st);
+  const u64 S = P->g.S;
+  const unsigned eb = (unsigned)((S + 255) / 256);
+  if (!rc && S) {
+    if (tri) widen_kernel<<<eb, 256, 0, st>>>(P->sa.T, reinterpret_cast<long long*>(tri), S);
+    if (c4) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E5, reinterpret_cast<long long*>(c4), S);
+    if (k4) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.K4, reinterpret_cast<long long*>(k4), S);
+    if (e7) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E7, reinterpret_cast<long long*>(e7), S);
+    if (e9) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E9, reinterpret_cast<long long*>(e9), S);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = EVOKE_ECUDA;
+  }
+  plan_free(P);
+  return rc;
+}
+
+int evoke_build_dag(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                    uint32_t* dag_rowptr, uint32_t* dag_colidx, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!dag_rowptr || (m && !dag_colidx)) return EVOKE_EINVAL;
+  int rc = check_csr(rowptr, colidx, n, m, st);
+  if (rc) return rc;
+  // the DAG alone: degrees, reverse slots, counts, scan, fill
+  const u64 S = 2 * m;
+  size_t bytes = sz<u32>(n) + sz<u32>(S) + sz<u32>(n) + sz<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1)) +
+                 sz<u32>(m) + sz<int>(4);
+  void* blk = nullptr;
+  if (cudaMallocAsync(&blk, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  Arena ar{static_cast<char*>(blk), bytes, 0, st};
+  Graph g{};
+  g.n = n;
+  g.S = S;
+  g.rowptr = rowptr;
+  g.col = colidx;
+  g.deg = ar.take<u32>(n);
+  g.rev = ar.take<u32>(S);
+  u32* cnt = ar.take<u32>(n);
+  void* scan_tmp = ar.take<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1));
+  g.dag_slot = ar.take<u32>(m);
+  int* status = ar.take<int>(4);
+  g.dag_ptr = dag_rowptr;
+  g.dag_col = dag_colidx;
+  if (ar.overflow) {
+    cudaFreeAsync(blk, st);
+    return EVOKE_ENOMEM;
+  }
+  cudaMemsetAsync(status, 0, sizeof(int) * 4, st);
+  phase("degrees", n ? 1 : 0, st, [&] { launch_degrees(g, st); });
+  phase("dag", n ? 5 : 0, st, [&] { launch_dag(g, cnt, scan_tmp, st); });
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(blk, st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? EVOKE_OK : EVOKE_ECUDA;
 }
 
 }  // extern "C"

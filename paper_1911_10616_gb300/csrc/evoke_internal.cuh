@@ -194,7 +194,10 @@ struct __align__(64) MapRec {
 };
 
 struct RootScratch {
-  MapRec* map;   // per CTA: n records, zero between roots
+  MapRec* map;   // per CTA: map_n records, zero between roots
+  const u32* comp_base;  // optional [n]: first id of each vertex's component (batches)
+  u32 map_n;     // records per CTA: n, or the largest component of a batch
+  int threads;   // 256 or 512 threads per CTA
   u32* touched;  // per CTA: n, ids touched by the current root
   u32* jlist;    // per CTA: n, middle vertices of the current root's 3-paths
   u32* order;    // n: roots in schedule order
@@ -205,13 +208,24 @@ struct RootScratch {
   u64* cycles;   // optional [n]: cycles per root
   int ctas;
 };
-size_t root_scratch_bytes(u32 n, int ctas);
+size_t root_scratch_bytes(u32 map_n, int ctas);
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
                            u32* pref, u32 pref_stride, cudaStream_t st);
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
                  cudaStream_t st);
-void launch_k5(const Graph& g, u64* acc, u32 max_outdeg, cudaStream_t st);
+struct K5Config {
+  size_t smem;
+  u32 smax;
+  u32 blocks;
+};
+K5Config k5_configure(u32 max_outdeg);  // host-side set-up (kernel attributes)
+void launch_k5(const Graph& g, u64* acc, const K5Config& c, cudaStream_t st);
+void launch_k4_known(const Graph& g, const SlotArrays& sa, u64* acc, u64 total, cudaStream_t st);
+void launch_union_csr(const u32* rowptr_cat, const u32* col_cat, const long long* vtx_off,
+                      const long long* edge_off, u32 G, u32 n, u64 S, u32* rowptr, u32* col,
+                      u32* comp_base, cudaStream_t st);
+void launch_max_component(const long long* vtx_off, u32 G, u32* out, cudaStream_t st);
 void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);

@@ -161,7 +161,62 @@ __global__ void scan_apply_kernel(const TIn* in, u64 count, const u64* __restric
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[count] = (TOut)sums[gridDim.x];
 }
 
+// ---- batches: concatenated per-graph CSRs -> one CSR of their disjoint union --
+__device__ __forceinline__ u32 graph_of(const long long* off, u32 G, u64 x) {
+  // largest g < G with off[g] <= x
+  u32 lo = 0, hi = G;
+  while (hi - lo > 1) {
+    u32 mid = lo + ((hi - lo) >> 1);
+    if ((u64)off[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void union_rows_kernel(const u32* __restrict__ rowptr_cat, const long long* vtx_off,
+                                  const long long* edge_off, u32 G, u32 n, u32* __restrict__ rowptr,
+                                  u32* __restrict__ comp_base) {
+  const u32 v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v > n) return;
+  if (v == n) {
+    rowptr[n] = (u32)edge_off[G];
+    return;
+  }
+  const u32 g = graph_of(vtx_off, G, v);
+  const u32 local = v - (u32)vtx_off[g];
+  // graph g's rowptr occupies entries vtx_off[g] + g .. vtx_off[g+1] + g
+  rowptr[v] = (u32)edge_off[g] + rowptr_cat[vtx_off[g] + g + local];
+  comp_base[v] = (u32)vtx_off[g];
+}
+
+__global__ void union_cols_kernel(const u32* __restrict__ col_cat, const long long* vtx_off,
+                                  const long long* edge_off, u32 G, u64 S, u32* __restrict__ col) {
+  const u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const u32 g = graph_of(edge_off, G, s);
+  col[s] = col_cat[s] + (u32)vtx_off[g];
+}
+
+__global__ void max_component_kernel(const long long* vtx_off, u32 G, u32* out) {
+  const u32 g = blockIdx.x * blockDim.x + threadIdx.x;
+  u32 v = g < G ? (u32)(vtx_off[g + 1] - vtx_off[g]) : 0;
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
+}
+
 }  // namespace
+
+void launch_union_csr(const u32* rowptr_cat, const u32* col_cat, const long long* vtx_off,
+                      const long long* edge_off, u32 G, u32 n, u64 S, u32* rowptr, u32* col,
+                      u32* comp_base, cudaStream_t st) {
+  union_rows_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(rowptr_cat, vtx_off, edge_off, G, n,
+                                                          rowptr, comp_base);
+  if (S) union_cols_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(col_cat, vtx_off, edge_off, G, S, col);
+}
+
+void launch_max_component(const long long* vtx_off, u32 G, u32* out, cudaStream_t st) {
+  if (G) max_component_kernel<<<(G + 255) / 256, 256, 0, st>>>(vtx_off, G, out);
+}
 
 // the thread-major tile layout of scan_apply (thread t owns items
 // [t*8, t*8+8)) differs from scan_reduce's strided layout; both only need the

@@ -19,7 +19,6 @@
 
 namespace {
 
-constexpr int kRootThreads = 512;
 constexpr u32 kFlag = 0x80000000u;
 constexpr u32 kCnt = 0x7fffffffu;
 
@@ -127,18 +126,19 @@ __device__ __forceinline__ u64 seg_sum(u32 key, u64 val, bool* is_tail) {
   return val;
 }
 
-__global__ void __launch_bounds__(kRootThreads)
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
 root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* pref_all,
             u32 pref_stride) {
   const u32 n = g.n;
-  const u64 off = (u64)blockIdx.x * n;
+  const u64 off = (u64)blockIdx.x * rs.map_n;
   MapRec* __restrict__ M = rs.map + off;
   u32* __restrict__ touched = rs.touched + off;
   u32* __restrict__ jlist = rs.jlist + off;
-  __shared__ u32 s_wpref[kRootThreads / 32][33];
-  __shared__ u32 s_wsab[kRootThreads / 32][32];
-  __shared__ u32 s_wsa[kRootThreads / 32][32];
-  __shared__ u32 s_wsb[kRootThreads / 32][32];
+  __shared__ u32 s_wpref[kThreads / 32][33];
+  __shared__ u32 s_wsab[kThreads / 32][32];
+  __shared__ u32 s_wsa[kThreads / 32][32];
+  __shared__ u32 s_wsb[kThreads / 32][32];
   __shared__ u32 s_pref[kSmemPref + 1];
   __shared__ u32 s_root, s_nt, s_nj, s_carry;
   __shared__ u64 s_red[32];
@@ -157,6 +157,8 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     const u32 qi = s_root;
     if (qi >= n) break;
     const u32 u = rs.order[qi];
+    // maps are indexed by id within the root's component (batched graphs)
+    const u32 cbase = rs.comp_base ? rs.comp_base[u] : 0u;
     const u32 ub = g.rowptr[u], ue = g.rowptr[u + 1], du = ue - ub;
     u32* pref = du + 1 <= kSmemPref ? s_pref : gpref;
     long long tp = 0;
@@ -166,7 +168,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     // phase 0: mark the neighbours, prefix of their degrees
     for (u32 i = threadIdx.x; i < du; i += blockDim.x) {
       const u32 v = g.col[ub + i];
-      M[v].W = kFlag;
+      M[v - cbase].W = kFlag;
       touched[atomicAdd(&s_nt, 1u)] = v;
     }
     neighbour_degree_prefix(g, ub, du, pref, s_red, &s_carry);
@@ -181,7 +183,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 x = g.col[t];
       if (x == u) continue;
       const bool in_in = prec(g.deg, u, v) && prec(g.deg, x, v);
-      const u64 old = atomicAdd(reinterpret_cast<u64*>(&M[x].W), in_in ? 1ull : (1ull | (1ull << 32)));
+      const u64 old = atomicAdd(reinterpret_cast<u64*>(&M[x - cbase].W), in_in ? 1ull : (1ull | (1ull << 32)));
       if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
     }
     __syncthreads();
@@ -242,10 +244,10 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
             const u32 tsab = s_wsab[wid][lo];
             const u32 y = g.col[g.tl[g.tl_ptr[tsab] + (it - s_wpref[wid][lo])]];
             if (y != u) {
-              const u64 wy2 = (u64)((long long)(M[y].W & kCnt) - 2);
+              const u64 wy2 = (u64)((long long)(M[y - cbase].W & kCnt) - 2);
               a63 += wy2;                // DM63: sum over diamonds of W(u,y) - 2
               if (u < y) {
-                atomicAdd(&M[y].D, 1u);  // D(u,y), needed for y > u only
+                atomicAdd(&M[y - cbase].D, 1u);  // D(u,y), needed for y > u only
                 add = wy2;
                 key = lo;
               }
@@ -272,10 +274,10 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         const u32 x = g.dag_col[p];
         if (x == u) continue;
         const u32 sk = g.dag_slot[p];
-        const u64 old = atomicAdd(&M[x].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
+        const u64 old = atomicAdd(&M[x - cbase].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
         if ((old >> 32) == 0) jlist[atomicAdd(&s_nj, 1u)] = x;
         const u32 mm = sa.Mmid[sk];
-        if (mm) atomicAdd(&M[x].X, mm);
+        if (mm) atomicAdd(&M[x - cbase].X, mm);
       }
     }
     __syncthreads();
@@ -290,23 +292,23 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 nj = s_nj;
       for (u32 idx = wid; idx < nj; idx += nw) {
         const u32 j = jlist[idx];
-        const u64 ry = M[j].RY;
+        const u64 ry = M[j - cbase].RY;
         const u64 R = ry >> 32, Yj = ry & 0xffffffffull;
-        const bool jl = (M[j].W & kFlag) != 0;
+        const bool jl = (M[j - cbase].W & kFlag) != 0;
         const bool j_to_u = jl && prec(g.deg, j, u);
         u64 z = 0;
         for (u32 p = g.dag_ptr[j] + lane; p < g.dag_ptr[j + 1]; p += 32) {
           const u32 i = g.dag_col[p];
           if (i == u) continue;
-          const u32 wn = M[i].Wn;
+          const u32 wn = M[i - cbase].Wn;
           if (!wn) continue;
           z += wn;
-          atomicAdd(&M[i].P, R);
-          if (jl) atomicAdd(&M[i].Pjl, R);
+          atomicAdd(&M[i - cbase].P, R);
+          if (jl) atomicAdd(&M[i - cbase].Pjl, R);
         }
         z = warp_sum(z);
         if (lane == 0) {
-          M[j].Z = z;
+          M[j - cbase].Z = z;
           const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (j_to_u ? 1 : 0);
           const u64 cj = R * z - Yj + (j_to_u ? R : 0) - (jl ? 2 * R * dpj : 0);
           if (cj) atomicAdd(&acc[(u64)A_C5 * n + j], cj);
@@ -338,15 +340,15 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (x == u) {
             valid = false;
           } else {
-            const u32 wr = M[x].W;
+            const u32 wr = M[x - cbase].W;
             const long long wx = wr & kCnt;
             e5 = (u64)(wx - 1);
             a51 += ((u64)sa.T[t] - ((wr & kFlag) ? 1 : 0)) * (u64)(wx - 1);
             if (u < x) {
               b49 = c2(wx - 1);
-              b62 = M[x].D;
+              b62 = M[x - cbase].D;
             }
-            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = M[x].P;
+            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = M[x - cbase].P;
           }
         }
         seg_atomic_add(sa.E5, s, valid, e5);
@@ -363,8 +365,8 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       for (u32 p = g.dag_ptr[k] + lane; p < g.dag_ptr[k + 1]; p += 32) {
         const u32 j = g.dag_col[p];
         if (j == u) continue;
-        u64 t = M[j].Z;
-        if (M[j].W & kFlag) {
+        u64 t = M[j - cbase].Z;
+        if (M[j - cbase].W & kFlag) {
           const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (prec(g.deg, j, u) ? 1 : 0);
           t -= dpj;
         }
@@ -392,7 +394,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 nt = s_nt;
       for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
         const u32 x = touched[idx];
-        const MapRec r = M[x];
+        const MapRec r = M[x - cbase];
         const u32 wr = r.W;
         const long long w = wr & kCnt;
         const u64 cw2 = c2(w);
@@ -406,7 +408,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (ci) atomicAdd(&acc[(u64)A_C5 * n + x], ci);
           a5 += ci;
         }
-        M[x] = MapRec{};
+        M[x - cbase] = MapRec{};
       }
       a8 = block_sum(a8, s_red);
       if (threadIdx.x == 0) acc[(u64)A_DM8 * n + u] = a8;
@@ -700,7 +702,10 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
                            u32* pref, u32 pref_stride, cudaStream_t st) {
   if (!g.n) return;
   cudaMemsetAsync(rs.head, 0, sizeof(u32), st);
-  root_kernel<<<rs.ctas, kRootThreads, 0, st>>>(g, sa, acc, rs, pref, pref_stride);
+  if (rs.threads == 256)
+    root_kernel<256><<<rs.ctas, 256, 0, st>>>(g, sa, acc, rs, pref, pref_stride);
+  else
+    root_kernel<512><<<rs.ctas, 512, 0, st>>>(g, sa, acc, rs, pref, pref_stride);
 }
 
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
@@ -709,21 +714,28 @@ void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, 
   link_kernel<<<warps / kLinkWarps, kLinkWarps * 32, 0, st>>>(g, sa, scratch, dmax);
 }
 
-void launch_k5(const Graph& g, u64* acc, u32 max_outdeg, cudaStream_t st) {
-  const u32 m = (u32)(g.S / 2);
-  if (!m || max_outdeg < 3) return;
+K5Config k5_configure(u32 max_outdeg) {
+  K5Config c{};
+  if (max_outdeg < 3) return c;
   // shared memory per warp: S list + |S| x ceil(|S|/32) bitmap words
   u32 smax = (max_outdeg + 31) / 32 * 32;
   const u32 cap = 640;
   if (smax > cap) smax = cap;
   const size_t per_warp = ((size_t)smax + (size_t)smax * ((smax + 31) / 32)) * sizeof(u32);
-  const size_t smem = per_warp * kK5Warps;
-  cudaFuncSetAttribute(k5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  c.smem = per_warp * kK5Warps;
+  c.smax = smax;
+  cudaFuncSetAttribute(k5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_kernel, kK5Warps * 32, smem);
-  const u32 blocks = (u32)sms * (u32)(per_sm > 0 ? per_sm : 1) * 4;
-  k5_kernel<<<blocks, kK5Warps * 32, smem, st>>>(g, acc, m, smax);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_kernel, kK5Warps * 32, c.smem);
+  c.blocks = (u32)sms * (u32)(per_sm > 0 ? per_sm : 1) * 4;
+  return c;
+}
+
+void launch_k5(const Graph& g, u64* acc, const K5Config& c, cudaStream_t st) {
+  const u32 m = (u32)(g.S / 2);
+  if (!m || !c.blocks) return;
+  k5_kernel<<<c.blocks, kK5Warps * 32, c.smem, st>>>(g, acc, m, c.smax);
 }

@@ -233,6 +233,12 @@ void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_
   tri_opp_kernel<2><<<blocks_for((u64)g.n * 32, 256), 256, 0, st>>>(g, sa, acc);
 }
 
+void launch_k4_known(const Graph& g, const SlotArrays& sa, u64* acc, u64 total, cudaStream_t st) {
+  if (!g.S) return;
+  if (total) k4_kernel<<<blocks_for(total, 256), 256, 0, st>>>(g, sa, acc, total);
+  halve_kernel<<<blocks_for(g.S, 256), 256, 0, st>>>(sa.K4, g.S);
+}
+
 void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {
   if (!g.S) return;
   u64 total = 0;
