@@ -42,6 +42,11 @@ WORKLOADS = {
                       "Chung-Lu n=100,000 m~1,000,000 exponent 2.1 degree cap 5,000"),
     "chung_lu_30k": (dict(kind="chung_lu", n=30_000, m=300_000, exponent=2.1, cap=1000),
                      "Chung-Lu n=30,000 m~300,000 exponent 2.1 degree cap 1,000"),
+    "batch_200k": (dict(kind="batch", graphs=200_000, nmin=10, nmax=500),
+                   "200,000 graphs, n ~ U[10,500], 1/3 each ER (avg degree 4-12), BA (m0 2-5), "
+                   "2-D RGG (avg degree 6); one CUDA-graph replay per step"),
+    "batch_20k": (dict(kind="batch", graphs=20_000, nmin=10, nmax=500),
+                  "20,000 graphs, n ~ U[10,500], 1/3 each ER / BA / RGG"),
 }
 
 
@@ -197,6 +202,241 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def timed(fn, steps, stream, barrier):
+    """Run fn() `steps` times between CUDA events on `stream`; seconds."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    barrier()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    barrier()
+    return a.elapsed_time(b) / 1000.0
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def roofline_of(phases, g, ev, rp, col, n, m, args):
+    peak, peak_kind = read_peaks()
+    if not phases:
+        return None
+    name, (nl, calls, ms) = max(phases.items(), key=lambda kv: kv[1][2])
+    per_launch_s = ms / 1000.0 / max(nl, 1)
+    ent = None
+    if name == "root" and g is not None and not args.no_roofline:
+        T_slot = ev.edge_orbits(rp, col, n, m)["T"].cpu().numpy()
+        ent = root_pass_entries(g, T_slot)
+        alg_bytes = 4 * ent["entries"]
+    else:
+        alg_bytes = 4 * (2 * m) + 8 * n  # lower bound: one read of the CSR
+    achieved = alg_bytes / per_launch_s / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "algorithmic_bytes": alg_bytes, "launch_ms": per_launch_s * 1000.0, "units": ent}
+
+
+def run_single(args, rank, world, dist, barrier):
+    import torch
+    import paper_1911_10616_gb300 as ev
+    from paper_1911_10616_gb300 import _lib
+
+    spec, desc = WORKLOADS[args.workload]
+    seed = 1 + rank
+    t0 = time.perf_counter()
+    g = make_graph(spec, seed)
+    gen_s = time.perf_counter() - t0
+    ev.load()
+    rp, col = ev.to_device(g)
+    n, m = g.n, g.m
+    stream = torch.cuda.current_stream()
+    plan = ev.Plan.single(rp, col, n, m, validate=True)
+    out = plan.new_output()
+    for _ in range(args.warmup):
+        plan.execute(out)
+    barrier()
+
+    # timed region: K executions of the whole pass sequence, inputs resident,
+    # per-phase CUDA events recorded on the launching stream
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    launches0 = _lib.launch_count()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t_run = timed(lambda: plan.execute_profiled(out), args.steps, stream, barrier)
+    _lib.profile_enable(False)
+    launches = _lib.launch_count() - launches0
+    phases = _lib.profile_read()
+    t_max = max_over_ranks(t_run, dist)
+    value = world * m * args.steps / t_max
+
+    # the same executions replayed as one CUDA graph each
+    plan.launch_graph(out)
+    t_graph = max_over_ranks(timed(lambda: plan.launch_graph(out), args.steps, stream, barrier), dist)
+
+    # end to end through the public one-shot API: pinned host CSR in, host counts out
+    e2e = None
+    if args.e2e_steps > 0:
+        h_rp = torch.from_numpy(g.rowptr.astype(np.uint32).view(np.int32)).pin_memory()
+        h_col = torch.from_numpy(g.col.astype(np.uint32).view(np.int32)).pin_memory()
+        h_out = torch.empty((n, 73), dtype=torch.int64).pin_memory()
+        d_rp = torch.empty_like(rp)
+        d_col = torch.empty_like(col)
+
+        def e2e_step():
+            d_rp.copy_(h_rp, non_blocking=True)
+            d_col.copy_(h_col, non_blocking=True)
+            ev.count_orbits(d_rp, d_col, n, m, out=out)
+            h_out.copy_(out, non_blocking=True)
+
+        e2e_t = max(max_over_ranks(timed(e2e_step, args.e2e_steps, stream, barrier), dist), 1e-12)
+        e2e = {"value": world * m * args.e2e_steps / e2e_t, "unit": UNIT,
+               "h2d_bytes_per_step": h_rp.numel() * 4 + h_col.numel() * 4,
+               "d2h_bytes_per_step": h_out.numel() * 8}
+    if rank != 0:
+        return None
+    info = plan.info()
+    roof = roofline_of(phases, g, ev, rp, col, n, m, args)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_oracle_baseline(args.workload, seed=1, budget_s=args.cpu_budget)
+            cpu.pop("seconds", None)
+        except Exception as exc:  # report, never fake
+            cpu = {"error": repr(exc)}
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": desc, "n": n, "m": m, "seed": seed,
+                   "parallelism": f"replicas{world}", "schedule": "degree-bucket",
+                   "l2": "working set (CSR + per-edge arrays, GBs) far larger than the 129 MB L2",
+                   "triangles": info["triangles"], "max_degree": info["max_degree"],
+                   "gen_s": round(gen_s, 1)},
+        "graph_replay": {"value": world * m * args.steps / t_graph, "unit": UNIT,
+                         "ms_per_step": 1000.0 * t_graph / args.steps},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "phases_ms": {k: round(v[2] / max(v[1], 1), 3) for k, v in sorted(phases.items())},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+
+
+def run_batch(args, rank, world, dist, barrier):
+    import torch
+    import paper_1911_10616_gb300 as ev
+    from paper_1911_10616_gb300 import _lib, graphgen as gg
+
+    spec, desc = WORKLOADS[args.workload]
+    seed = 1 + rank
+    t0 = time.perf_counter()
+    rpc, colc, vo, eo = gg.small_graph_batch_tensors(spec["graphs"], spec["nmin"], spec["nmax"],
+                                                     seed, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    G = vo.numel() - 1
+    N = int(vo[-1].item())
+    M = int(eo[-1].item()) // 2
+    ev.load()
+    stream = torch.cuda.current_stream()
+    plan = ev.Plan.batch(rpc, colc, vo, eo, validate=True)
+    out = plan.new_output()
+    info = plan.info()
+
+    # autotune the per-root pass: threads per CTA and persistent CTAs
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cands = [(512, 2 * sms), (256, 4 * sms), (512, sms), (256, 2 * sms)]
+    tune = []
+    for th, ct in cands:
+        if ct > info["root_ctas_max"]:
+            continue
+        plan.set_tuning(th, ct)
+        plan.execute(out)
+        tune.append((timed(lambda: plan.execute(out), 1, stream, barrier), th, ct))
+    best = min(tune)
+    plan.set_tuning(best[1], best[2])
+
+    for _ in range(args.warmup):
+        plan.launch_graph(out)
+    barrier()
+    launches0 = _lib.launch_count()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t_run = timed(lambda: plan.launch_graph(out), args.steps, stream, barrier)
+    launches = _lib.launch_count() - launches0
+    t_max = max_over_ranks(t_run, dist)
+    value = world * G * args.steps / t_max
+
+    # per-phase times of one profiled execution (for the roofline)
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    timed(lambda: plan.execute_profiled(out), 1, stream, barrier)
+    _lib.profile_enable(False)
+    phases = _lib.profile_read()
+
+    # one launch sequence per graph, on a prefix of the batch
+    k = min(args.per_graph_sample, G)
+    h_vo, h_eo = vo.cpu().numpy(), eo.cpu().numpy()
+    h_rp, h_col = rpc.cpu().numpy(), colc.cpu().numpy()
+    singles = []
+    for gi in range(k):
+        gr = gg.batch_graph(h_rp, h_col, h_vo, h_eo, gi)
+        singles.append((ev.to_device(gr), gr.n, gr.m))
+    o1 = torch.empty((int(h_vo[k] - h_vo[0]) if k else 0, 73), dtype=torch.int64, device="cuda")
+
+    def per_graph():
+        for (drp, dcol), n1, m1 in singles:
+            ev.count_orbits(drp, dcol, n1, m1, out=o1[: n1] if n1 else o1[:0])
+
+    t_single = timed(per_graph, 1, stream, barrier) if k else None
+    if rank != 0:
+        return None
+    roof = roofline_of(phases, None, ev, None, None, N, M, args)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        th = oracle.max_threads()
+        kk = min(60, G)
+        t0 = time.perf_counter()
+        for gi in range(kk):
+            oracle.formulas(gg.batch_graph(h_rp, h_col, h_vo, h_eo, gi), th)
+        dt = time.perf_counter() - t0
+        cpu = {"value": kk / dt, "unit": "graphs/s", "cores": th, "kind": "oracle",
+               "sample": f"the first {kk} graphs of the batch"}
+    return {
+        "metric": "batched graphs/s, all 73 vertex orbits", "value": value, "unit": "graphs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": desc, "graphs": G, "vertices": N, "edges": M, "seed": seed,
+                   "parallelism": f"replicas{world}", "max_component": info["max_component"],
+                   "triangles": info["triangles"], "device_bytes": info["device_bytes"],
+                   "tuned_root": {"threads": best[1], "ctas": best[2]},
+                   "tuning_s": {f"{th}x{ct}": round(t, 4) for t, th, ct in tune},
+                   "l2": "working set (tens of GB) far larger than the 129 MB L2",
+                   "gen_s": round(gen_s, 1)},
+        "edges_per_s": world * M * args.steps / t_max,
+        "one_launch_per_graph": ({"graphs": k, "value": k / t_single, "unit": "graphs/s",
+                                  "speedup_of_batched": (value / world) / (k / t_single)}
+                                 if t_single else None),
+        "e2e": None,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "phases_ms": {k2: round(v[2] / max(v[1], 1), 3) for k2, v in sorted(phases.items())},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +447,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--per-graph-sample", type=int, default=500)
     ap.add_argument("--no-roofline", action="store_true",
                     help="skip the extra pass that sizes the roofline's algorithmic bytes")
     args = ap.parse_args()
@@ -220,9 +461,6 @@ def main():
         return
 
     import torch
-    import paper_1911_10616_gb300 as ev
-    from paper_1911_10616_gb300 import _lib
-
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -234,125 +472,12 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    spec, desc = WORKLOADS[args.workload]
-    seed = 1 + rank
-    t0 = time.perf_counter()
-    g = make_graph(spec, seed)
-    gen_s = time.perf_counter() - t0
-    ev.load()
-    rp, col = ev.to_device(g)
-    n, m = g.n, g.m
-    out = torch.empty((n, 73), dtype=torch.int64, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    # warm-up (also validates the input once)
-    for i in range(args.warmup):
-        ev.count_orbits(rp, col, n, m, out=out, validate=(i == 0))
-    barrier()
-
-    # timed region: inputs resident, K steps, CUDA events on the stream
-    _lib.profile_reset()
-    _lib.profile_enable(True)
-    launches0 = _lib.launch_count()
-    ev_a = torch.cuda.Event(enable_timing=True)
-    ev_b = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        ev_a.record(stream)
-        for _ in range(args.steps):
-            ev.count_orbits(rp, col, n, m, out=out)
-        ev_b.record(stream)
-        barrier()
-    _lib.profile_enable(False)
-    launches = _lib.launch_count() - launches0
-    phases = _lib.profile_read()
-    ms_total = ev_a.elapsed_time(ev_b)
-    t_local = ms_total / 1000.0
-    if dist is not None:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    if WORKLOADS[args.workload][0]["kind"] == "batch":
+        line = run_batch(args, rank, world, dist, barrier)
     else:
-        t_max = t_local
-    value = world * m * args.steps / t_max
-
-    # end to end through the public API: pinned host CSR in, host counts out
-    h_rp = torch.from_numpy(g.rowptr.astype(np.uint32).view(np.int32)).pin_memory()
-    h_col = torch.from_numpy(g.col.astype(np.uint32).view(np.int32)).pin_memory()
-    h_out = torch.empty((n, 73), dtype=torch.int64).pin_memory()
-    d_rp = torch.empty_like(rp)
-    d_col = torch.empty_like(col)
-    barrier()
-    e_a = torch.cuda.Event(enable_timing=True)
-    e_b = torch.cuda.Event(enable_timing=True)
-    e_a.record(stream)
-    for _ in range(args.e2e_steps):
-        d_rp.copy_(h_rp, non_blocking=True)
-        d_col.copy_(h_col, non_blocking=True)
-        ev.count_orbits(d_rp, d_col, n, m, out=out)
-        h_out.copy_(out, non_blocking=True)
-    e_b.record(stream)
-    barrier()
-    e2e_t = max(e_a.elapsed_time(e_b) / 1000.0, 1e-12)
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    h2d = h_rp.numel() * 4 + h_col.numel() * 4
-    d2h = h_out.numel() * 8
-
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
-
-    # roofline of the dominant pass
-    peak, peak_kind = read_peaks()
-    dom = max(phases.items(), key=lambda kv: kv[1][2]) if phases else None
-    roof = None
-    if dom is not None:
-        name, (nl, calls, ms) = dom
-        per_launch_s = ms / 1000.0 / max(nl, 1)
-        want_units = name == "root" and not args.no_roofline
-        T_slot = ev.edge_orbits(rp, col, n, m)["T"].cpu().numpy() if want_units else None
-        if want_units:
-            ent = root_pass_entries(g, T_slot)
-            alg_bytes = 4 * ent["entries"]
-        else:
-            ent = None
-            alg_bytes = 4 * (2 * m) + 8 * n  # lower bound: one read of the CSR
-        achieved = alg_bytes / per_launch_s / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_kind, "algorithmic_bytes": alg_bytes,
-                "launch_ms": per_launch_s * 1000.0, "units": ent}
-
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        try:
-            cpu = cpu_oracle_baseline(args.workload, seed=1, budget_s=args.cpu_budget)
-            cpu.pop("seconds", None)
-        except Exception as exc:  # report, never fake
-            cpu = {"error": repr(exc)}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic",
-        "config": {"workload": desc, "n": n, "m": m, "seed": seed, "parallelism": f"replicas{world}",
-                   "l2": "working set (CSR + per-edge arrays, GBs) far larger than the 129 MB L2",
-                   "gen_s": round(gen_s, 1)},
-        "e2e": ({"value": world * m * args.e2e_steps / e2e_t, "unit": UNIT,
-                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-                if args.e2e_steps > 0 else None),
-        "gpu_launches": launches,
-        "roofline": roof,
-        "phases_ms": {k: round(v[2] / max(v[1], 1), 3) for k, v in sorted(phases.items())},
-        "cpu_baseline": cpu,
-        "clocks": clk.summary(),
-    }
-    print(json.dumps(line), flush=True)
+        line = run_single(args, rank, world, dist, barrier)
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -129,6 +129,9 @@ int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_c
                             const evoke_opts* opts, void* stream, evoke_plan** plan);
 int evoke_plan_execute(evoke_plan* plan, int64_t* out, void* stream);
 int evoke_plan_launch_graph(evoke_plan* plan, int64_t* out, void* stream);
+/* evoke_plan_execute with every phase bracketed by the profiler's events
+ * (when evoke_profile_enable is on); same kernels, same results. */
+int evoke_plan_execute_profiled(evoke_plan* plan, int64_t* out, void* stream);
 int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* stats);
 /* Autotuning hook: threads per CTA (256 or 512) and the number of persistent
  * CTAs of the per-root pass, at most the number the plan was created with. */

@@ -27,7 +27,7 @@ _ERRORS = {
 SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
            "evoke_build_dag_noalloc", "evoke_edge_orbits", "evoke_orbit_matrix",
            "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
-           "evoke_plan_launch_graph", "evoke_plan_info", "evoke_plan_set_tuning",
+           "evoke_plan_launch_graph", "evoke_plan_execute_profiled", "evoke_plan_info", "evoke_plan_set_tuning",
            "evoke_plan_destroy",
            "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
            "evoke_launch_count", "evoke_strerror", "evoke_version")
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         lib.evoke_plan_create_batch.restype = ctypes.c_int
         lib.evoke_plan_execute.argtypes = [vp, vp, vp]
         lib.evoke_plan_launch_graph.argtypes = [vp, vp, vp]
+        lib.evoke_plan_execute_profiled.argtypes = [vp, vp, vp]
         lib.evoke_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
         lib.evoke_plan_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.evoke_plan_destroy.argtypes = [vp]
@@ -234,6 +235,13 @@ class Plan:
     def execute(self, out, stream=None):
         _check(load().evoke_plan_execute(self._h, _ptr(out), _stream_handle(stream)),
                "evoke_plan_execute")
+        return out
+
+    def execute_profiled(self, out, stream=None):
+        """execute() with the library's per-phase CUDA events (see
+        profile_enable); the same kernels."""
+        _check(load().evoke_plan_execute_profiled(self._h, _ptr(out), _stream_handle(stream)),
+               "evoke_plan_execute_profiled")
         return out
 
     def launch_graph(self, out, stream=None):

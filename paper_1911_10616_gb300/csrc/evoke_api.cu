@@ -783,6 +783,13 @@ int evoke_plan_execute(evoke_plan* plan, int64_t* out, void* stream) {
   return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
 }
 
+int evoke_plan_execute_profiled(evoke_plan* plan, int64_t* out, void* stream) {
+  if (!plan || (plan->n && !out)) return EVOKE_EINVAL;
+  execute(plan, reinterpret_cast<long long*>(out), static_cast<cudaStream_t>(stream),
+          /*timed=*/true);
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
+
 int evoke_plan_launch_graph(evoke_plan* plan, int64_t* out, void* stream) {
   if (!plan || (plan->n && !out)) return EVOKE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -19,12 +19,15 @@ generators stand in for them):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 __all__ = [
     "Graph", "csr_from_pairs", "er_gnm", "er_gnp", "chung_lu", "rmat",
     "barabasi_albert", "random_geometric", "complete", "star", "cycle", "path",
     "from_edge_list", "relabel", "small_graph_batch", "concat_batch",
+    "small_graph_batch_tensors", "batch_graph",
 ]
 
 
@@ -271,3 +274,160 @@ def concat_batch(graphs):
     rowptr_cat = np.concatenate([g.rowptr.astype(np.uint32) for g in graphs]) if G else np.zeros(0, np.uint32)
     col_cat = np.concatenate([g.col for g in graphs]) if G else np.zeros(0, np.uint32)
     return rowptr_cat, col_cat, vtx_off, edge_off
+
+
+def _batch_csr_torch(ns, gid, a, b):
+    """Per-graph local edges (graph id, a, b) as torch int64 tensors ->
+    batch CSR (rowptr_cat int32-bits-of-uint32, col_cat, vtx_off int64,
+    edge_off int64), loops and duplicates removed."""
+    import torch
+    dev = ns.device
+    G = ns.numel()
+    vtx_off = torch.zeros(G + 1, dtype=torch.int64, device=dev)
+    vtx_off[1:] = torch.cumsum(ns, 0)
+    keep = a != b
+    gid, a, b = gid[keep], a[keep], b[keep]
+    lo = torch.minimum(a, b)
+    hi = torch.maximum(a, b)
+    N = int(vtx_off[-1].item())
+    key = torch.unique((vtx_off[gid] + lo) * N + (vtx_off[gid] + hi))
+    ga = key // N
+    gb = key % N
+    src = torch.cat([ga, gb])
+    dst = torch.cat([gb, ga])
+    order = torch.argsort(src * N + dst)
+    src, dst = src[order], dst[order]
+    deg = torch.bincount(src, minlength=N)
+    grow = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+    grow[1:] = torch.cumsum(deg, 0)
+    edge_off = grow[vtx_off]
+    reps = ns + 1
+    gid_rows = torch.repeat_interleave(torch.arange(G, device=dev), reps)
+    first_row = torch.zeros(G, dtype=torch.int64, device=dev)
+    first_row[1:] = torch.cumsum(reps, 0)[:-1]
+    local = torch.arange(gid_rows.numel(), device=dev) - first_row[gid_rows]
+    rowptr_cat = grow[vtx_off[gid_rows] + local] - edge_off[gid_rows]
+    gid_slots = torch.repeat_interleave(torch.arange(G, device=dev), edge_off[1:] - edge_off[:-1])
+    col_cat = dst - vtx_off[gid_slots]
+    return (rowptr_cat.to(torch.int32), col_cat.to(torch.int32), vtx_off, edge_off)
+
+
+def small_graph_batch_tensors(count: int, nmin: int, nmax: int, seed: int, device="cpu"):
+    """The many-small-graphs workload in batch CSR form, generated with torch
+    on `device` (seeded): graph g has n_g ~ U[nmin, nmax] vertices;
+    g % 3 == 0: Erdos-Renyi with average degree ~ U[4, 12] (distinct uniform
+    pairs); g % 3 == 1: Barabasi-Albert, each new vertex joins m0 ~ U{2..5}
+    distinct targets drawn in proportion to degree (seeded by a star on the
+    first m0 vertices); g % 3 == 2: 2-D random geometric graph in the unit
+    square with radius sqrt(6 / (pi (n-1))) (average degree about 6).
+    Returns (rowptr_cat, col_cat, vtx_off, edge_off) torch tensors; ids are
+    uint32 bit patterns in int32 tensors."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    dev = torch.device(device)
+    rnd = lambda *shape: torch.rand(*shape, generator=gen, device=dev)
+    ns = (nmin + (rnd(count) * (nmax - nmin + 1)).long()).clamp_(nmin, nmax)
+    fam = torch.arange(count, device=dev) % 3
+    pg, pa, pb = [], [], []
+
+    # Erdos-Renyi
+    er = torch.nonzero(fam == 0).flatten()
+    if er.numel():
+        n_er = ns[er]
+        deg = 4.0 + 8.0 * rnd(er.numel())
+        want = torch.minimum(torch.round(deg * n_er / 2).long(), n_er * (n_er - 1) // 2)
+        draws = (want.double() * 1.4 + 8).long()
+        gid = torch.repeat_interleave(er, draws)
+        nn = ns[gid]
+        x = (rnd(gid.numel()) * nn).long()
+        y = (rnd(gid.numel()) * nn).long()
+        ok = x != y
+        gid, x, y = gid[ok], x[ok], y[ok]
+        lo, hi = torch.minimum(x, y), torch.maximum(x, y)
+        key = torch.unique((gid * 1024 + lo) * 1024 + hi)
+        gid, lo, hi = key // (1024 * 1024), (key // 1024) % 1024, key % 1024
+        pri = rnd(gid.numel())
+        order = torch.argsort(gid.double() * 2.0 + pri)  # by graph, random within
+        gid, lo, hi = gid[order], lo[order], hi[order]
+        cnt = torch.bincount(gid, minlength=count)
+        start = torch.zeros(count, dtype=torch.long, device=dev)
+        start[1:] = torch.cumsum(cnt, 0)[:-1]
+        rank = torch.arange(gid.numel(), device=dev) - start[gid]
+        cap = torch.zeros(count, dtype=torch.long, device=dev)
+        cap[er] = want
+        sel = rank < cap[gid]
+        pg.append(gid[sel]); pa.append(lo[sel]); pb.append(hi[sel])
+
+    # Barabasi-Albert, all graphs grown in lock-step
+    ba = torch.nonzero(fam == 1).flatten()
+    if ba.numel():
+        B = ba.numel()
+        m0 = 2 + (rnd(B) * 4).long().clamp_(0, 3)
+        nb = ns[ba]
+        L = int((2 * m0 * nb).max().item()) + 16
+        rep = torch.zeros((B, L), dtype=torch.long, device=dev)
+        ln = torch.zeros(B, dtype=torch.long, device=dev)
+        rows = torch.arange(B, device=dev)
+        for k in range(1, 5):  # seed star: 0 - k for k < m0
+            s = rows[m0 > k]
+            pg.append(ba[s]); pa.append(torch.zeros_like(s)); pb.append(torch.full_like(s, k))
+            rep[s, ln[s]] = 0
+            rep[s, ln[s] + 1] = k
+            ln[s] += 2
+        kcol = torch.arange(5, device=dev)
+        for t in range(2, int(nb.max().item())):
+            act = rows[(nb > t) & (m0 <= t)]
+            if act.numel() == 0:
+                continue
+            k = m0[act]
+            need = kcol[None, :] < k[:, None]                 # (A, 5)
+            tg = torch.full((act.numel(), 5), -1, dtype=torch.long, device=dev)
+            todo = need.clone()
+            for _ in range(64):
+                if not bool(todo.any()):
+                    break
+                idx = (rnd(act.numel(), 5) * ln[act][:, None]).long()
+                cand = torch.gather(rep[act], 1, idx)
+                tg = torch.where(todo, cand, tg)
+                # a slot is a duplicate if an earlier slot of its row holds the same target
+                same = (tg[:, :, None] == tg[:, None, :]) & need[:, :, None] & need[:, None, :]
+                earlier = torch.tril(torch.ones(5, 5, dtype=torch.bool, device=dev), -1)
+                todo = (same & earlier[None]).any(2)
+            r_i, c_i = torch.nonzero(need, as_tuple=True)
+            gsel = act[r_i]
+            pg.append(ba[gsel]); pa.append(torch.full_like(gsel, t)); pb.append(tg[r_i, c_i])
+            pos = ln[gsel] + 2 * c_i
+            rep[gsel, pos] = tg[r_i, c_i]
+            rep[gsel, pos + 1] = t
+            ln[act] += 2 * k
+
+    # random geometric, grouped by size
+    rg = torch.nonzero(fam == 2).flatten()
+    if rg.numel():
+        sizes = torch.unique(ns[rg]).tolist()
+        for nval in sizes:
+            grp = rg[ns[rg] == nval]
+            n = int(nval)
+            pts = rnd(grp.numel(), n, 2)
+            d2 = torch.cdist(pts.double(), pts.double()) ** 2
+            r2 = 6.0 / (math.pi * (n - 1))
+            iu = torch.triu(torch.ones(n, n, dtype=torch.bool, device=dev), 1)
+            gi, ii, jj = torch.nonzero((d2 <= r2) & iu[None], as_tuple=True)
+            pg.append(grp[gi]); pa.append(ii); pb.append(jj)
+
+    gid = torch.cat(pg) if pg else torch.zeros(0, dtype=torch.long, device=dev)
+    a = torch.cat(pa) if pa else torch.zeros(0, dtype=torch.long, device=dev)
+    b = torch.cat(pb) if pb else torch.zeros(0, dtype=torch.long, device=dev)
+    return _batch_csr_torch(ns, gid.long(), a.long(), b.long())
+
+
+def batch_graph(rowptr_cat, col_cat, vtx_off, edge_off, g: int) -> Graph:
+    """Graph g of a batch (numpy arrays or CPU tensors) in CSR form."""
+    rowptr_cat, col_cat, vtx_off, edge_off = (np.asarray(x) for x in
+                                              (rowptr_cat, col_cat, vtx_off, edge_off))
+    n = int(vtx_off[g + 1] - vtx_off[g])
+    r0 = int(vtx_off[g] + g)
+    rp = rowptr_cat[r0:r0 + n + 1].astype(np.uint32).astype(np.int64)
+    col = col_cat[int(edge_off[g]):int(edge_off[g + 1])].astype(np.uint32)
+    return Graph(n, rp, col)
