@@ -45,6 +45,14 @@ WORKLOADS = {
     "batch_200k": (dict(kind="batch", graphs=200_000, nmin=10, nmax=500),
                    "200,000 graphs, n ~ U[10,500], 1/3 each ER (avg degree 4-12), BA (m0 2-5), "
                    "2-D RGG (avg degree 6); one CUDA-graph replay per step"),
+    "rmat_20_learned": (dict(kind="learned", scale=20, edge_factor=16, cap=20000, train=20,
+                             train_scales=(16, 17, 18)),
+                        "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+                        "degree cap 20,000; learned vs degree-bucket schedule (MLP 4-32-32-1 "
+                        "trained on 20 R-MAT scale 16-18 graphs)"),
+    "rmat_16_learned": (dict(kind="learned", scale=16, edge_factor=16, cap=20000, train=4,
+                             train_scales=(13, 14)),
+                        "R-MAT scale 16 (small learned-schedule check)"),
     "batch_20k": (dict(kind="batch", graphs=20_000, nmin=10, nmax=500),
                   "20,000 graphs, n ~ U[10,500], 1/3 each ER / BA / RGG"),
 }
@@ -437,6 +445,87 @@ def run_batch(args, rank, world, dist, barrier):
     }
 
 
+def run_learned(args, rank, world, dist, barrier):
+    """Learned vs degree-bucket schedule on one R-MAT graph (same plan, same
+    counts; only the persistent root queue's order differs)."""
+    import torch
+    import paper_1911_10616_gb300 as ev
+    from paper_1911_10616_gb300 import _lib, graphgen as gg, learned
+
+    spec, desc = WORKLOADS[args.workload]
+    ev.load()
+    t0 = time.perf_counter()
+    train_graphs = learned.training_graphs(spec["train"], scales=spec["train_scales"],
+                                           cap=spec["cap"], seed0=100 + 1000 * rank)
+    data = [learned.measure(g)[:2] for g in train_graphs]
+    collect_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params, losses = learned.train(data, epochs=40, batch=4096)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    g = gg.rmat(spec["scale"], spec["edge_factor"], *learned.RMAT_ABC, seed=1 + rank,
+                cap=spec["cap"])
+    rp, col = ev.to_device(g)
+    n, m = g.n, g.m
+    stream = torch.cuda.current_stream()
+    plan = ev.Plan.single(rp, col, n, m, validate=True)
+    out = plan.new_output()
+    res = {}
+    for name, model in (("degree_bucket", None), ("learned", params)):
+        plan.set_model(model)
+        for _ in range(args.warmup):
+            plan.execute(out)
+        _lib.profile_reset()
+        _lib.profile_enable(True)
+        t = timed(lambda: plan.execute_profiled(out), args.steps, stream, barrier)
+        _lib.profile_enable(False)
+        ph = _lib.profile_read()
+        cyc, ends = plan.root_timing(out)
+        e = ends.cpu().numpy().astype(np.float64)
+        res[name] = {"ms_per_step": 1000.0 * t / args.steps,
+                     "root_ms": ph["root"][2] / max(ph["root"][1], 1),
+                     "tail_ms": float((e.max() - e.min()) / 1e6),
+                     "cycles": cyc.cpu().numpy()}
+    X, y, _ = learned.measure(g)
+    pred = _lib.mlp_forward(X, params).cpu().numpy()
+    meas = y.cpu().numpy()
+    busy = g.degrees() > 0
+    work = learned.wedge_work(g)
+    A = np.vstack([np.log2(1 + work[busy]), np.ones(busy.sum())]).T
+    coef = np.linalg.lstsq(A, meas[busy], rcond=None)[0]
+    ctas = plan.info()["root_ctas"]
+    c = res["degree_bucket"]["cycles"].astype(np.float64)
+    sim = {k: learned.list_schedule_makespan(c, o, ctas) / max(c.sum() / ctas, c.max())
+           for k, o in (("learned", np.argsort(-pred, kind="stable")),
+                        ("degree_bucket", np.argsort(-work, kind="stable")),
+                        ("vertex_id", np.arange(n)))}
+    plan.destroy()
+    if rank != 0:
+        return None
+    t_l = res["learned"]["ms_per_step"] / 1000.0
+    return {
+        "metric": METRIC + " (learned schedule)", "value": world * m / t_l, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["learned"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "m": m, "max_degree": int(g.degrees().max()),
+                   "training_vertices": int(sum(d[0].shape[0] for d in data)),
+                   "collect_s": round(collect_s, 1), "train_s": round(train_s, 2),
+                   "loss_first_last": [losses[0], losses[-1]]},
+        "learned_vs_degree_bucket": {
+            "step_speedup": res["degree_bucket"]["ms_per_step"] / res["learned"]["ms_per_step"],
+            "root_pass_speedup": res["degree_bucket"]["root_ms"] / res["learned"]["root_ms"],
+            "degree_bucket": {k: v for k, v in res["degree_bucket"].items() if k != "cycles"},
+            "learned": {k: v for k, v in res["learned"].items() if k != "cycles"},
+            "spearman_log2_cycles": {"learned": learned.spearman(pred[busy], meas[busy]),
+                                     "wedge_work": learned.spearman(work[busy], meas[busy])},
+            "mae_log2_cycles": {"learned": float(np.abs(pred[busy] - meas[busy]).mean()),
+                                "wedge_work_affine": float(np.abs(A @ coef - meas[busy]).mean())},
+            "simulated_makespan_over_lower_bound": sim},
+        "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -474,6 +563,8 @@ def main():
 
     if WORKLOADS[args.workload][0]["kind"] == "batch":
         line = run_batch(args, rank, world, dist, barrier)
+    elif WORKLOADS[args.workload][0]["kind"] == "learned":
+        line = run_learned(args, rank, world, dist, barrier)
     else:
         line = run_single(args, rank, world, dist, barrier)
     if line is not None:

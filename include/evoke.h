@@ -139,6 +139,48 @@ int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_c
 int evoke_plan_destroy(evoke_plan* plan);
 
 /*
+ * Learned work model.  The paper has no counterpart: it runs one thread and
+ * schedules nothing.  Here a 4 -> 32 -> 32 -> 1 ReLU MLP in FP32 (1249
+ * parameters, layout W1[32][4], b1[32], W2[32][32], b2[32], W3[32], b3)
+ * predicts log2 of the cycles the per-root pass spends on each vertex from
+ * log2(1 + x) of (DAG out-degree, neighbour degree sum = wedges rooted at
+ * the vertex, sum of the out-neighbours' out-degrees, triangles at the
+ * vertex).  With a model attached, the plan
+ * orders its persistent root queue by that prediction (largest first)
+ * instead of by the wedge-work estimate sum_{v in N(u)} d(v); the counts are
+ * identical either way.  All arrays are DEVICE memory.
+ *
+ * evoke_plan_set_model  : attach params (1249 floats, must stay alive), or
+ *                         NULL to return to the degree-bucket schedule.
+ * evoke_plan_features   : X[n*4] features of every vertex (valid after one
+ *                         execution of the plan).
+ * evoke_plan_root_timing: one execution that also records, per vertex, the
+ *                         clock64 cycles the per-root pass spent on it
+ *                         (root_cycles[n]) and, per CTA, the global timer
+ *                         (ns) when it ran out of roots (cta_end_ns[ctas]);
+ *                         either may be NULL; out may be NULL.
+ * evoke_mlp_forward     : y[N] = MLP(X[N*4]).
+ * evoke_mlp_grad        : grad[1249] of the mean squared error of MLP(X)
+ *                         against T[N], and the loss (*loss, device float).
+ * evoke_mlp_train       : `epochs` passes of Adam (lr, beta 0.9 / 0.999) over
+ *                         contiguous mini-batches of `batch` samples; params
+ *                         updated in place, state = 2*1249 floats (zero at
+ *                         start), scratch = 1280 + epochs floats, loss_out =
+ *                         HOST float[epochs] (mean batch loss summed per
+ *                         epoch) or NULL.  Synchronises `stream` if loss_out.
+ */
+int evoke_plan_set_model(evoke_plan* plan, const float* params);
+int evoke_plan_features(evoke_plan* plan, float* X, void* stream);
+int evoke_plan_root_timing(evoke_plan* plan, uint64_t* root_cycles, uint64_t* cta_end_ns,
+                           int64_t* out, void* stream);
+int evoke_mlp_forward(const float* X, uint32_t N, const float* params, float* y, void* stream);
+int evoke_mlp_grad(const float* X, const float* T, uint32_t N, const float* params, float* grad,
+                   float* loss, void* stream);
+int evoke_mlp_train(const float* X, const float* T, uint32_t N, float* params, float* state,
+                    int32_t epochs, int32_t batch, float lr, float* loss_out, float* scratch,
+                    void* stream);
+
+/*
  * evoke_build_dag -- the degree-ordered DAG of Sec. 2: edge u -> v iff
  * d(u) < d(v), or d(u) = d(v) and u < v.
  *   dag_rowptr : device uint32[n+1] (written), dag_colidx : device

@@ -28,7 +28,8 @@ SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
            "evoke_build_dag_noalloc", "evoke_edge_orbits", "evoke_orbit_matrix",
            "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
            "evoke_plan_launch_graph", "evoke_plan_execute_profiled", "evoke_plan_info", "evoke_plan_set_tuning",
-           "evoke_plan_destroy",
+           "evoke_plan_destroy", "evoke_plan_set_model", "evoke_plan_features",
+           "evoke_plan_root_timing", "evoke_mlp_forward", "evoke_mlp_grad", "evoke_mlp_train",
            "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
            "evoke_launch_count", "evoke_strerror", "evoke_version")
 
@@ -102,6 +103,13 @@ def load(build_if_missing: bool = True):
         lib.evoke_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
         lib.evoke_plan_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.evoke_plan_destroy.argtypes = [vp]
+        lib.evoke_plan_set_model.argtypes = [vp, vp]
+        lib.evoke_plan_features.argtypes = [vp, vp, vp]
+        lib.evoke_plan_root_timing.argtypes = [vp, vp, vp, vp, vp]
+        lib.evoke_mlp_forward.argtypes = [vp, u32, vp, vp, vp]
+        lib.evoke_mlp_grad.argtypes = [vp, vp, u32, vp, vp, vp, vp]
+        lib.evoke_mlp_train.argtypes = [vp, vp, u32, vp, vp, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp, vp]
         lib.evoke_profile_enable.argtypes = [ctypes.c_int]
         lib.evoke_profile_read.argtypes = [ctypes.POINTER(PhaseTime), ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int)]
@@ -258,6 +266,30 @@ class Plan:
         _check(load().evoke_plan_set_tuning(self._h, int(root_threads), int(root_ctas)),
                "evoke_plan_set_tuning")
 
+    def set_model(self, params):
+        """Attach MLP parameters (float32 CUDA tensor of 1249) or None."""
+        self._model = params
+        _check(load().evoke_plan_set_model(self._h, _ptr(params) if params is not None else None),
+               "evoke_plan_set_model")
+
+    def features(self, stream=None):
+        import torch
+        X = torch.empty((self.n, 4), dtype=torch.float32, device=self._inputs[0].device)
+        _check(load().evoke_plan_features(self._h, _ptr(X), _stream_handle(stream)),
+               "evoke_plan_features")
+        return X
+
+    def root_timing(self, out=None, stream=None):
+        """One execution recording per-vertex root-pass cycles and per-CTA end
+        times; returns (cycles int64 [n], cta_end_ns int64 [ctas])."""
+        import torch
+        dev = self._inputs[0].device
+        cyc = torch.zeros(self.n, dtype=torch.int64, device=dev)
+        ends = torch.zeros(max(self.info()["root_ctas_max"], 1), dtype=torch.int64, device=dev)
+        _check(load().evoke_plan_root_timing(self._h, _ptr(cyc), _ptr(ends), _ptr(out),
+                                             _stream_handle(stream)), "evoke_plan_root_timing")
+        return cyc, ends[: self.info()["root_ctas"]]
+
     def destroy(self):
         if self._h:
             load().evoke_plan_destroy(self._h)
@@ -336,3 +368,36 @@ def profile_read():
 
 def launch_count() -> int:
     return int(load().evoke_launch_count())
+
+
+MLP_PARAMS = 1249
+
+
+def mlp_forward(X, params, stream=None):
+    import torch
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(load().evoke_mlp_forward(_ptr(X), X.shape[0], _ptr(params), _ptr(y),
+                                    _stream_handle(stream)), "evoke_mlp_forward")
+    return y
+
+
+def mlp_grad(X, T, params, stream=None):
+    import torch
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    _check(load().evoke_mlp_grad(_ptr(X), _ptr(T), X.shape[0], _ptr(params), _ptr(g), _ptr(loss),
+                                 _stream_handle(stream)), "evoke_mlp_grad")
+    return g, loss
+
+
+def mlp_train(X, T, params, epochs: int, batch: int, lr: float, state=None, stream=None):
+    """Adam training on device, params updated in place; returns per-epoch losses."""
+    import torch
+    if state is None:
+        state = torch.zeros(2 * MLP_PARAMS, dtype=torch.float32, device=X.device)
+    scratch = torch.zeros(1280 + epochs, dtype=torch.float32, device=X.device)
+    losses = (ctypes.c_float * epochs)()
+    _check(load().evoke_mlp_train(_ptr(X), _ptr(T), X.shape[0], _ptr(params), _ptr(state),
+                                  epochs, batch, float(lr), losses, _ptr(scratch),
+                                  _stream_handle(stream)), "evoke_mlp_train")
+    return [float(v) for v in losses], state

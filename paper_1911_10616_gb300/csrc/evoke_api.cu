@@ -369,6 +369,11 @@ struct evoke_plan {
   cudaStream_t st = nullptr;
   int launches_per_exec = 0;
   int ctas_alloc = 0;     // CTAs the root maps were allocated for
+  // learned schedule
+  const float* model = nullptr;  // device, 1249 floats
+  float* feat = nullptr;         // n x 4
+  float* prio = nullptr;         // n
+  void* model_block = nullptr;
   // CUDA graph of one execution
   cudaGraphExec_t gexec = nullptr;
   long long* gexec_out = nullptr;
@@ -487,7 +492,7 @@ int plan_stage2(evoke_plan* P) {
   }();
   size_t bytes = sz<u32>(P->ntri_entries) + 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) +
                  sz<u64>((size_t)NACC * n) + root_scratch_bytes(map_n, ctas) + 256 * 8 +
-                 sz<u32>(n) + sz<u32>(64) + sz<u32>(4) +
+                 sz<u32>(n) + sz<u32>(256) + sz<u32>(4) +
                  sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * dmax);
   if (cudaMallocAsync(&P->block2, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   P->bytes2 = bytes;
@@ -513,9 +518,10 @@ int plan_stage2(evoke_plan* P) {
   rs.touched = ar.take<u32>((size_t)ctas * map_n);
   rs.jlist = ar.take<u32>((size_t)ctas * map_n);
   rs.order = ar.take<u32>(n);
-  rs.bucket_cnt = ar.take<u32>(64);
+  rs.bucket_cnt = ar.take<u32>(256);
   rs.head = ar.take<u32>(4);
   rs.tsrc = P->acc + (size_t)A_TSRC * n;
+  rs.cta_end = nullptr;
   rs.prof = root_profile ? ar.take<u64>(8) : nullptr;
   rs.cycles = nullptr;
   P->pref = ar.take<u32>((size_t)ctas * P->pref_stride);
@@ -565,7 +571,17 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
   run("vsum1", nl, [&] { launch_vsum1(g, sa, acc, st); });
   run("tri_opp1", nl, [&] { launch_tri_opp1(g, sa, acc, st); });
   run("k4", (P->ntri_entries ? 1 : 0) + sl, [&] { launch_k4_known(g, sa, acc, P->ntri_entries, st); });
-  run("schedule", 3 * nl, [&] { launch_schedule(g, acc, P->rs, st); });
+  if (P->model) {
+    run("model", 2 * nl, [&] {
+      launch_features(g, acc, P->feat, st);
+      launch_mlp_forward(P->feat, n, P->model, P->prio, st);
+    });
+    run("schedule", 3 * nl, [&] {
+      launch_priority_schedule(P->prio, n, P->rs.bucket_cnt, P->rs.head, P->rs.order, st);
+    });
+  } else {
+    run("schedule", 3 * nl, [&] { launch_schedule(g, acc, P->rs, st); });
+  }
   run("root", nl, [&] { launch_root_with_pref(g, sa, acc, P->rs, P->pref, P->pref_stride, st); });
   run("link", sl, [&] {
     launch_link(g, sa, P->link_scratch, P->cfg.link_warps, std::max<u32>(P->dmax, 1), st);
@@ -583,6 +599,7 @@ int count_launches(const evoke_plan* P, bool with_out) {
   if (P->batch) k += 1 + sl;
   k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + sl + nl + nl;
   k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl + sl + (P->k5.blocks ? 1 : 0) + nl + nl + nl;
+  if (P->model) k += 2 * nl;
   if (with_out) k += nl;
   return k;
 }
@@ -590,6 +607,7 @@ int count_launches(const evoke_plan* P, bool with_out) {
 void plan_free(evoke_plan* P) {
   if (!P) return;
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->model_block) cudaFreeAsync(P->model_block, P->st);
   if (P->block) cudaFreeAsync(P->block, P->st);
   if (P->block2) cudaFreeAsync(P->block2, P->st);
   cudaStreamSynchronize(P->st);
@@ -855,6 +873,98 @@ int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_c
   plan->rs.threads = root_threads;
   plan->rs.ctas = root_ctas;
   return EVOKE_OK;
+}
+
+int evoke_plan_set_model(evoke_plan* plan, const float* params) {
+  if (!plan) return EVOKE_EINVAL;
+  if (plan->gexec) {
+    cudaGraphExecDestroy(plan->gexec);
+    plan->gexec = nullptr;
+  }
+  plan->model = params;
+  if (params && !plan->model_block && plan->n) {
+    if (cudaMallocAsync(&plan->model_block, sizeof(float) * 5 * (size_t)plan->n + 256, plan->st) !=
+        cudaSuccess)
+      return EVOKE_ENOMEM;
+    plan->feat = static_cast<float*>(plan->model_block);
+    plan->prio = plan->feat + 4 * (size_t)plan->n;
+    if (cudaStreamSynchronize(plan->st) != cudaSuccess) return EVOKE_ECUDA;
+  }
+  plan->launches_per_exec = count_launches(plan, true);
+  return EVOKE_OK;
+}
+
+int evoke_plan_features(evoke_plan* plan, float* X, void* stream) {
+  if (!plan || (plan->n && !X)) return EVOKE_EINVAL;
+  launch_features(plan->g, plan->acc, X, static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
+
+int evoke_plan_root_timing(evoke_plan* plan, uint64_t* root_cycles, uint64_t* cta_end_ns,
+                           int64_t* out, void* stream) {
+  if (!plan) return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  plan->rs.cycles = reinterpret_cast<u64*>(root_cycles);
+  plan->rs.cta_end = reinterpret_cast<u64*>(cta_end_ns);
+  execute(plan, reinterpret_cast<long long*>(out), st, /*timed=*/false);
+  plan->rs.cycles = nullptr;
+  plan->rs.cta_end = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches += (unsigned long long)count_launches(plan, out != nullptr);
+  }
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
+
+int evoke_mlp_forward(const float* X, uint32_t N, const float* params, float* y, void* stream) {
+  if ((N && (!X || !y)) || !params) return EVOKE_EINVAL;
+  launch_mlp_forward(X, N, params, y, static_cast<cudaStream_t>(stream));
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches += N ? 1 : 0;
+  }
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
+
+int evoke_mlp_grad(const float* X, const float* T, uint32_t N, const float* params, float* grad,
+                   float* loss, void* stream) {
+  if (!params || !grad || !loss || (N && (!X || !T))) return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(loss, 0, sizeof(float), st);
+  launch_mlp_grad(X, T, nullptr, 0, N, params, grad, loss, st);
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches += N ? 1 : 0;
+  }
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
+}
+
+int evoke_mlp_train(const float* X, const float* T, uint32_t N, float* params, float* state,
+                    int32_t epochs, int32_t batch, float lr, float* loss_out, float* scratch,
+                    void* stream) {
+  if (!X || !T || !params || !state || !scratch || N == 0 || epochs <= 0 || batch <= 0)
+    return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* grad = scratch;             // 1249
+  float* loss = scratch + 1280;      // epochs
+  cudaMemsetAsync(loss, 0, sizeof(float) * epochs, st);
+  int step = 0;
+  for (int e = 0; e < epochs; ++e) {
+    for (u32 lo = 0; lo < N; lo += (u32)batch) {
+      const u32 cnt = std::min<u32>((u32)batch, N - lo);
+      launch_mlp_grad(X, T, nullptr, lo, cnt, params, grad, loss + e, st);
+      launch_adam(params, grad, state, lr, ++step, st);
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_launches += 2ull * (unsigned long long)step;
+  }
+  if (loss_out) {
+    cudaMemcpyAsync(loss_out, loss, sizeof(float) * epochs, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
 }
 
 int evoke_plan_destroy(evoke_plan* plan) {

@@ -206,6 +206,7 @@ struct RootScratch {
   u64* tsrc;     // n: DAG triangles with the vertex as source
   u64* prof;     // optional [8]: cycles per phase (summed over roots)
   u64* cycles;   // optional [n]: cycles per root
+  u64* cta_end;  // optional [ctas]: global timer (ns) when each CTA ran out of roots
   int ctas;
 };
 size_t root_scratch_bytes(u32 map_n, int ctas);
@@ -231,3 +232,13 @@ void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t s
 void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);
 int upload_transform(const long long* A73x73);
 void launch_finalize(const Graph& g, const u64* acc, long long* out, cudaStream_t st);
+// learned work model
+int mlp_param_count();
+void launch_features(const Graph& g, const u64* acc, float* X, cudaStream_t st);
+void launch_mlp_forward(const float* X, u32 N, const float* params, float* y, cudaStream_t st);
+void launch_mlp_grad(const float* X, const float* T, const u32* idx, u32 lo, u32 cnt,
+                     const float* params, float* grad, float* loss, cudaStream_t st);
+void launch_adam(float* params, const float* grad, float* state, float lr, int step,
+                 cudaStream_t st);
+void launch_priority_schedule(const float* y, u32 n, u32* bucket_cnt, u32* head, u32* order,
+                              cudaStream_t st);

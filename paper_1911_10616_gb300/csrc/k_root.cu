@@ -155,7 +155,14 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     }
     __syncthreads();
     const u32 qi = s_root;
-    if (qi >= n) break;
+    if (qi >= n) {
+      if (rs.cta_end && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        rs.cta_end[blockIdx.x] = t;
+      }
+      break;
+    }
     const u32 u = rs.order[qi];
     // maps are indexed by id within the root's component (batched graphs)
     const u32 cbase = rs.comp_base ? rs.comp_base[u] : 0u;
