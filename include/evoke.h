@@ -48,7 +48,7 @@ extern "C" {
 #define EVOKE_ENOMEM 4       /* internal device allocation failed */
 #define EVOKE_ECUDA 5        /* a CUDA call or kernel launch failed */
 #define EVOKE_ETIMEOUT 6     /* a bounded device wait gave up */
-#define EVOKE_EOVERFLOW 7    /* reserved: checked-arithmetic builds */
+#define EVOKE_EOVERFLOW 7    /* an internal 32-bit count (3-paths per vertex pair) wrapped */
 
 typedef struct evoke_opts {
   int32_t validate;   /* nonzero: check the CSR invariants first (syncs the stream) */

@@ -403,9 +403,12 @@ void apply_config(evoke_plan* P, u32 map_n) {
   P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (P->rs.threads == 256 ? 4 : 2);
   // maps for up to 4 CTAs per SM when that is cheap, so that tuning can
   // raise the CTA count later
-  const size_t per_cta = (size_t)map_n * (sizeof(MapRec) + 2 * sizeof(u32));
+  const size_t per_cta = (size_t)map_n * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32));
   P->ctas_alloc = P->rs.ctas;
-  if ((size_t)sms * 4 * per_cta <= ((size_t)4 << 30)) P->ctas_alloc = std::max(P->ctas_alloc, sms * 4);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)4 << 30;
+  const size_t budget = std::min<size_t>(free_b / 3, (size_t)64 << 30);
+  if ((size_t)sms * 4 * per_cta <= budget) P->ctas_alloc = std::max(P->ctas_alloc, sms * 4);
 }
 
 // stage 1 buffers (graph-sized) and the sizing passes
@@ -490,7 +493,7 @@ int plan_stage2(evoke_plan* P) {
     const char* e = getenv("EVOKE_ROOT_PROFILE");
     return e && *e && *e != '0';
   }();
-  size_t bytes = sz<u32>(P->ntri_entries) + 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) +
+  size_t bytes = 2 * sz<u32>(P->ntri_entries) + 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) +
                  sz<u64>((size_t)NACC * n) + root_scratch_bytes(map_n, ctas) + 256 * 8 +
                  sz<u32>(n) + sz<u32>(256) + sz<u32>(4) +
                  sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * dmax);
@@ -498,6 +501,7 @@ int plan_stage2(evoke_plan* P) {
   P->bytes2 = bytes;
   Arena ar{static_cast<char*>(P->block2), bytes, 0, st};
   P->g.tl = ar.take<u32>(P->ntri_entries);
+  P->g.tlv = ar.take<u32>(P->ntri_entries);
   SlotArrays& sa = P->sa;
   sa.E5 = ar.take<u64>(S);
   sa.E7 = ar.take<u64>(S);
@@ -514,7 +518,9 @@ int plan_stage2(evoke_plan* P) {
   RootScratch& rs = P->rs;
   rs.map_n = map_n;
   rs.comp_base = P->batch ? P->comp_base : nullptr;
-  rs.map = ar.take<MapRec>((size_t)ctas * map_n);
+  rs.hot = ar.take<MapHot>((size_t)ctas * map_n);
+  rs.cold = ar.take<MapCold>((size_t)ctas * map_n);
+  rs.overflow = P->status + 1;
   rs.touched = ar.take<u32>((size_t)ctas * map_n);
   rs.jlist = ar.take<u32>((size_t)ctas * map_n);
   rs.order = ar.take<u32>(n);
@@ -539,6 +545,7 @@ void clear_accumulators(evoke_plan* P, cudaStream_t st) {
   const size_t slot_bytes = (char*)(P->sa.Mmid) - (char*)(P->sa.E5);  // E5 .. bc5 contiguous
   cudaMemsetAsync(P->sa.E5, 0, slot_bytes, st);
   cudaMemsetAsync(P->acc, 0, sizeof(u64) * (size_t)NACC * P->n, st);
+  cudaMemsetAsync(P->status + 1, 0, sizeof(int), st);  // 32-bit 3-path count overflow flag
   if (P->rs.prof) cudaMemsetAsync(P->rs.prof, 0, sizeof(u64) * 8, st);
   (void)S;
 }
@@ -658,9 +665,12 @@ int run_once(evoke_plan* P, long long* out, cudaStream_t st) {
                     "3-path push %.2f, wedges2+k %.2f, scan %.2f\n",
             pc[0] * 1e-9, pc[1] * 1e-9, pc[2] * 1e-9, pc[3] * 1e-9, pc[4] * 1e-9);
   }
+  int ovf = 0;
+  cudaMemcpyAsync(&ovf, P->status + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(st);
-  return (e == cudaSuccess && e2 == cudaSuccess) ? EVOKE_OK : EVOKE_ECUDA;
+  if (e != cudaSuccess || e2 != cudaSuccess) return EVOKE_ECUDA;
+  return ovf ? EVOKE_EOVERFLOW : EVOKE_OK;
 }
 
 }  // namespace

@@ -105,6 +105,7 @@ struct Graph {
   u32* dag_slot;         // m: CSR slot of each DAG edge (in the source row)
   u64* tl_ptr;           // S+1: triangle-list offsets per slot
   u32* tl;               // per slot (u,v): slots (u,x) for x in N(u)^N(v), ascending x
+  u32* tlv;              // the vertex ids x of the same entries
 };
 
 // device helpers ------------------------------------------------------------
@@ -178,23 +179,27 @@ void launch_tri_edge(const Graph& g, const SlotArrays& sa, cudaStream_t st);
 void launch_vsum1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_tri_opp1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
-// one record per vertex id in a CTA's dense 2-hop map (64 bytes: the fields
-// a root touches for one vertex share a pair of 32-byte sectors)
-struct __align__(64) MapRec {
-  u32 W;      // |N(root) ^ N(x)|, bit 31 flags a neighbour of the root
+// A CTA's dense 2-hop map, one entry per vertex id (within a component for
+// batches), split by access frequency: every wedge touches the 16-byte hot
+// record; only vertices on the root's directed 3-paths touch the cold one.
+struct __align__(16) MapHot {
+  u32 W;      // |N(root) ^ N(x)| in bits 0..29; bit 31: x ~ root; bit 30: cold record in use
   u32 Wn;     // wedges root-v-x not in-in at v (not root->v<-x)
-  u32 D;      // diamonds with root and x off the chord
+  u32 D;      // diamonds with root and x off the chord (x > root only)
+  u32 P;      // directed 3-paths root <- k -> j -> x
+};
+struct __align__(32) MapCold {
   u32 X;      // sum over k in N-(root)^N-(x) of #(k -> y -> x)
-  u64 spare;
-  u64 P;      // directed 3-paths root <- k -> j -> x
+  u32 pad;
   u64 RY;     // (|N-(root)^N-(x)| << 32) | sum over those k of #(k -> x -> y, k -> y)
-  u64 Pjl;    // those 3-paths with j ~ root
+  u64 Pjl;    // 3-paths root <- k -> j -> x with j ~ root
   u64 Z;      // sum of Wn over N+(x)
-  u64 pad;
 };
 
 struct RootScratch {
-  MapRec* map;   // per CTA: map_n records, zero between roots
+  MapHot* hot;   // per CTA: map_n records, zero between roots
+  MapCold* cold; // per CTA: map_n records, zero between roots
+  int* overflow; // set if a 32-bit 3-path count would wrap
   const u32* comp_base;  // optional [n]: first id of each vertex's component (batches)
   u32 map_n;     // records per CTA: n, or the largest component of a batch
   int threads;   // 256 or 512 threads per CTA

@@ -130,13 +130,16 @@ template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
 root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* pref_all,
             u32 pref_stride) {
+  constexpr u32 kCold = 0x40000000u;  // W bit 30: the cold record is in use
+  constexpr u32 kW = 0x3fffffffu;
   const u32 n = g.n;
   const u64 off = (u64)blockIdx.x * rs.map_n;
-  MapRec* __restrict__ M = rs.map + off;
+  MapHot* __restrict__ H = rs.hot + off;
+  MapCold* __restrict__ C = rs.cold + off;
   u32* __restrict__ touched = rs.touched + off;
   u32* __restrict__ jlist = rs.jlist + off;
   __shared__ u32 s_wpref[kThreads / 32][33];
-  __shared__ u32 s_wsab[kThreads / 32][32];
+  __shared__ u64 s_wsab[kThreads / 32][32];
   __shared__ u32 s_wsa[kThreads / 32][32];
   __shared__ u32 s_wsb[kThreads / 32][32];
   __shared__ u32 s_pref[kSmemPref + 1];
@@ -165,7 +168,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     }
     const u32 u = rs.order[qi];
     // maps are indexed by id within the root's component (batched graphs)
-    const u32 cbase = rs.comp_base ? rs.comp_base[u] : 0u;
+    const u32 cb = rs.comp_base ? rs.comp_base[u] : 0u;
     const u32 ub = g.rowptr[u], ue = g.rowptr[u + 1], du = ue - ub;
     u32* pref = du + 1 <= kSmemPref ? s_pref : gpref;
     long long tp = 0;
@@ -175,13 +178,13 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     // phase 0: mark the neighbours, prefix of their degrees
     for (u32 i = threadIdx.x; i < du; i += blockDim.x) {
       const u32 v = g.col[ub + i];
-      M[v - cbase].W = kFlag;
+      H[v - cb].W = kFlag;
       touched[atomicAdd(&s_nt, 1u)] = v;
     }
     neighbour_degree_prefix(g, ub, du, pref, s_red, &s_carry);
     const u32 total = pref[du];
 
-    // phase 1: wedges u - v - x.  W (low word) and Wn (high word) of the
+    // phase 1: wedges u - v - x.  W (low word) and Wn (high word) of the hot
     // record are bumped by one 64-bit atomic.
     for (u32 w = threadIdx.x; w < total; w += blockDim.x) {
       const u32 i = seg_find(pref, du + 1, w);
@@ -190,7 +193,8 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 x = g.col[t];
       if (x == u) continue;
       const bool in_in = prec(g.deg, u, v) && prec(g.deg, x, v);
-      const u64 old = atomicAdd(reinterpret_cast<u64*>(&M[x - cbase].W), in_in ? 1ull : (1ull | (1ull << 32)));
+      const u64 old = atomicAdd(reinterpret_cast<u64*>(&H[x - cb].W),
+                                in_in ? 1ull : (1ull | (1ull << 32)));
       if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
     }
     __syncthreads();
@@ -232,7 +236,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         }
         s_wpref[wid][lane + 1] = incl;
         if (lane == 0) s_wpref[wid][0] = 0;
-        s_wsab[wid][lane] = sab;
+        s_wsab[wid][lane] = len ? g.tl_ptr[sab] : 0;
         s_wsa[wid][lane] = sa_;
         s_wsb[wid][lane] = sb;
         __syncwarp();
@@ -248,13 +252,12 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
               if (s_wpref[wid][mid] <= it) lo = mid;
               else hi = mid;
             }
-            const u32 tsab = s_wsab[wid][lo];
-            const u32 y = g.col[g.tl[g.tl_ptr[tsab] + (it - s_wpref[wid][lo])]];
+            const u32 y = g.tlv[s_wsab[wid][lo] + (it - s_wpref[wid][lo])];
             if (y != u) {
-              const u64 wy2 = (u64)((long long)(M[y - cbase].W & kCnt) - 2);
-              a63 += wy2;                // DM63: sum over diamonds of W(u,y) - 2
+              const u64 wy2 = (u64)((long long)(H[y - cb].W & kW) - 2);
+              a63 += wy2;                 // DM63: sum over diamonds of W(u,y) - 2
               if (u < y) {
-                atomicAdd(&M[y - cbase].D, 1u);  // D(u,y), needed for y > u only
+                atomicAdd(&H[y - cb].D, 1u);  // D(u,y), needed for y > u only
                 add = wy2;
                 key = lo;
               }
@@ -281,10 +284,13 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         const u32 x = g.dag_col[p];
         if (x == u) continue;
         const u32 sk = g.dag_slot[p];
-        const u64 old = atomicAdd(&M[x - cbase].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
-        if ((old >> 32) == 0) jlist[atomicAdd(&s_nj, 1u)] = x;
+        const u64 old = atomicAdd(&C[x - cb].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
+        if ((old >> 32) == 0) {
+          jlist[atomicAdd(&s_nj, 1u)] = x;
+          atomicOr(&H[x - cb].W, kCold);
+        }
         const u32 mm = sa.Mmid[sk];
-        if (mm) atomicAdd(&M[x - cbase].X, mm);
+        if (mm) atomicAdd(&C[x - cb].X, mm);
       }
     }
     __syncthreads();
@@ -299,23 +305,27 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 nj = s_nj;
       for (u32 idx = wid; idx < nj; idx += nw) {
         const u32 j = jlist[idx];
-        const u64 ry = M[j - cbase].RY;
+        const u64 ry = C[j - cb].RY;
         const u64 R = ry >> 32, Yj = ry & 0xffffffffull;
-        const bool jl = (M[j - cbase].W & kFlag) != 0;
+        const bool jl = (H[j - cb].W & kFlag) != 0;
         const bool j_to_u = jl && prec(g.deg, j, u);
         u64 z = 0;
         for (u32 p = g.dag_ptr[j] + lane; p < g.dag_ptr[j + 1]; p += 32) {
           const u32 i = g.dag_col[p];
           if (i == u) continue;
-          const u32 wn = M[i - cbase].Wn;
+          const u32 wn = H[i - cb].Wn;
           if (!wn) continue;
           z += wn;
-          atomicAdd(&M[i - cbase].P, R);
-          if (jl) atomicAdd(&M[i - cbase].Pjl, R);
+          const u32 old = atomicAdd(&H[i - cb].P, (u32)R);
+          if (old + (u32)R < old) *rs.overflow = 1;
+          if (jl) {
+            atomicAdd(&C[i - cb].Pjl, R);
+            if (!(H[i - cb].W & kCold)) atomicOr(&H[i - cb].W, kCold);
+          }
         }
         z = warp_sum(z);
         if (lane == 0) {
-          M[j - cbase].Z = z;
+          C[j - cb].Z = z;
           const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (j_to_u ? 1 : 0);
           const u64 cj = R * z - Yj + (j_to_u ? R : 0) - (jl ? 2 * R * dpj : 0);
           if (cj) atomicAdd(&acc[(u64)A_C5 * n + j], cj);
@@ -347,15 +357,15 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (x == u) {
             valid = false;
           } else {
-            const u32 wr = M[x - cbase].W;
-            const long long wx = wr & kCnt;
+            const MapHot h = H[x - cb];
+            const long long wx = h.W & kW;
             e5 = (u64)(wx - 1);
-            a51 += ((u64)sa.T[t] - ((wr & kFlag) ? 1 : 0)) * (u64)(wx - 1);
+            a51 += ((u64)sa.T[t] - ((h.W & kFlag) ? 1 : 0)) * (u64)(wx - 1);
             if (u < x) {
               b49 = c2(wx - 1);
-              b62 = M[x - cbase].D;
+              b62 = h.D;
             }
-            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = M[x - cbase].P;
+            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = h.P;
           }
         }
         seg_atomic_add(sa.E5, s, valid, e5);
@@ -372,8 +382,8 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       for (u32 p = g.dag_ptr[k] + lane; p < g.dag_ptr[k + 1]; p += 32) {
         const u32 j = g.dag_col[p];
         if (j == u) continue;
-        u64 t = M[j - cbase].Z;
-        if (M[j - cbase].W & kFlag) {
+        u64 t = C[j - cb].Z;
+        if (H[j - cb].W & kFlag) {
           const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (prec(g.deg, j, u) ? 1 : 0);
           t -= dpj;
         }
@@ -401,21 +411,28 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 nt = s_nt;
       for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
         const u32 x = touched[idx];
-        const MapRec r = M[x - cbase];
-        const u32 wr = r.W;
-        const long long w = wr & kCnt;
+        const MapHot h = H[x - cb];
+        const long long w = h.W & kW;
         const u64 cw2 = c2(w);
         a8 += cw2;
         a36 += cw2 * (u64)((long long)g.deg[x] - 2);
         a50 += c3(w);
-        if (r.P | r.X) {
-          const bool u_to_x = (wr & kFlag) && prec(g.deg, u, x);
-          const u64 rx = r.RY >> 32;
-          const u64 ci = r.P * (u64)r.Wn - ((u64)r.X - (u_to_x ? rx : 0)) - r.Pjl;
+        if (h.W & kCold) {
+          const MapCold c = C[x - cb];
+          if (h.P | c.X) {
+            const bool u_to_x = (h.W & kFlag) && prec(g.deg, u, x);
+            const u64 rx = c.RY >> 32;
+            const u64 ci = (u64)h.P * (u64)h.Wn - ((u64)c.X - (u_to_x ? rx : 0)) - c.Pjl;
+            if (ci) atomicAdd(&acc[(u64)A_C5 * n + x], ci);
+            a5 += ci;
+          }
+          C[x - cb] = MapCold{};
+        } else if (h.P) {
+          const u64 ci = (u64)h.P * (u64)h.Wn;
           if (ci) atomicAdd(&acc[(u64)A_C5 * n + x], ci);
           a5 += ci;
         }
-        M[x - cbase] = MapRec{};
+        H[x - cb] = MapHot{};
       }
       a8 = block_sum(a8, s_red);
       if (threadIdx.x == 0) acc[(u64)A_DM8 * n + u] = a8;
@@ -692,8 +709,8 @@ k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
 
 }  // namespace
 
-size_t root_scratch_bytes(u32 n, int ctas) {
-  return (size_t)ctas * n * (sizeof(MapRec) + 2 * sizeof(u32)) + 16 * 256;
+size_t root_scratch_bytes(u32 map_n, int ctas) {
+  return (size_t)ctas * map_n * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32)) + 16 * 256;
 }
 
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st) {

@@ -51,6 +51,8 @@ __global__ void tri_kernel(Graph g, u32* __restrict__ T, u32 m) {
       if (kFill) {
         g.tl[o1 + cnt] = i;
         g.tl[o2 + cnt] = lo;
+        g.tlv[o1 + cnt] = x;
+        g.tlv[o2 + cnt] = x;
       }
       ++cnt;
     }
@@ -187,7 +189,7 @@ __global__ void k4_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, u64 tot
     if (x < y) ++i;
     else if (y < x) ++j;
     else {
-      const u32 apex = g.col[x];
+      const u32 apex = g.tlv[i];  // vertex id of entry i of tl(a,b)
       if (k4 > 1) atomicAdd(&acc[(u64)A_S70 * n + apex], (u64)(k4 - 1));
       atomicAdd(&acc[(u64)A_S66 * n + apex], tsum);
       ++i;
