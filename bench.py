@@ -45,6 +45,8 @@ WORKLOADS = {
     "batch_200k": (dict(kind="batch", graphs=200_000, nmin=10, nmax=500),
                    "200,000 graphs, n ~ U[10,500], 1/3 each ER (avg degree 4-12), BA (m0 2-5), "
                    "2-D RGG (avg degree 6); one CUDA-graph replay per step"),
+    "rmat_20": (dict(kind="rmat", scale=20, edge_factor=16, cap=20000),
+                "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), degree cap 20,000"),
     "rmat_20_learned": (dict(kind="learned", scale=20, edge_factor=16, cap=20000, train=20,
                              train_scales=(16, 17, 18)),
                         "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
@@ -60,6 +62,8 @@ WORKLOADS = {
 
 def make_graph(spec, seed):
     from paper_1911_10616_gb300 import graphgen as gg
+    if spec["kind"] == "rmat":
+        return gg.rmat(spec["scale"], spec["edge_factor"], 0.57, 0.19, 0.19, seed, cap=spec["cap"])
     if spec["kind"] == "chung_lu":
         return gg.chung_lu(spec["n"], spec["m"], spec["exponent"], spec["cap"], seed)
     if spec["kind"] == "er":

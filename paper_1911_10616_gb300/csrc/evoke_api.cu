@@ -496,7 +496,7 @@ int plan_stage2(evoke_plan* P) {
   size_t bytes = 2 * sz<u32>(P->ntri_entries) + 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) +
                  sz<u64>((size_t)NACC * n) + root_scratch_bytes(map_n, ctas) + 256 * 8 +
                  sz<u32>(n) + sz<u32>(256) + sz<u32>(4) +
-                 sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * dmax);
+                 sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * 2 * dmax);
   if (cudaMallocAsync(&P->block2, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   P->bytes2 = bytes;
   Arena ar{static_cast<char*>(P->block2), bytes, 0, st};
@@ -531,11 +531,12 @@ int plan_stage2(evoke_plan* P) {
   rs.prof = root_profile ? ar.take<u64>(8) : nullptr;
   rs.cycles = nullptr;
   P->pref = ar.take<u32>((size_t)ctas * P->pref_stride);
-  P->link_scratch = ar.take<u32>((size_t)link_warps * dmax);
+  P->link_scratch = ar.take<u32>((size_t)link_warps * 2 * dmax);  // counters + partner list
   if (ar.overflow) return EVOKE_ENOMEM;
   // maps and scratch rows are left zeroed by the kernels that use them
   cudaMemsetAsync(P->block2, 0, ar.used, st);
   P->k5 = k5_configure(P->max_outdeg);
+  link_configure();
   return EVOKE_OK;
 }
 

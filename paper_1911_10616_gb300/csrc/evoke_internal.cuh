@@ -218,6 +218,7 @@ size_t root_scratch_bytes(u32 map_n, int ctas);
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
                            u32* pref, u32 pref_stride, cudaStream_t st);
+void link_configure();  // host-side set-up (kernel attributes)
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
                  cudaStream_t st);
 struct K5Config {

@@ -480,24 +480,34 @@ __global__ void sched_scatter_kernel(const u64* __restrict__ work, u32 n, u32* c
 
 // --- wheel pass: 4-cycles through a inside N(u), for every slot (u,a) ------
 // (orbits 68 and 69: a wheel is a hub plus a 4-cycle in the hub's
-// neighbourhood).  W_c = number of 2-paths a - b - c inside N(u); the
-// 4-cycles through a are sum_c C(W_c, 2), accumulated as the sum of the
-// counter value before each increment.  One warp per slot (u,a); the warp
-// walks the concatenated triangle lists of the b's 32 at a time.  Counters
-// are 16-bit halves of shared-memory words when d(u) <= kLinkSmem (then
-// W_c < 2^16), else 32-bit words of the warp's global scratch row.
+// neighbourhood).  W_ac = number of 2-paths a - b - c inside N(u), and the
+// 4-cycles through a are sum_{c != a} C(W_ac, 2).  W is symmetric, so the
+// pass for a counts only partners c > a (slot order = id order; each chord
+// list is entered by binary search), keeps sum_{c > a} C(W_ac, 2) and credits
+// C(W_ac, 2) to c once per pair.  One warp per slot (u,a); the warp walks the
+// concatenated list tails of the b's 32 at a time.  Counters are 16-bit
+// halves of shared-memory words when d(u) <= kLinkSmem (then W < 2^16), else
+// 32-bit words of the warp's global scratch row; touched partners are listed
+// so that the counters can be credited and cleared.
 constexpr int kLinkWarps = 8;
 constexpr u32 kLinkSmem = 2048;
 
+constexpr size_t kLinkDynSmem = (size_t)kLinkWarps * (kLinkSmem / 2 + kLinkSmem) * sizeof(u32);
+
 __global__ void __launch_bounds__(kLinkWarps * 32)
 link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
-  __shared__ u32 s_map[kLinkWarps][kLinkSmem / 2];
+  extern __shared__ u32 link_smem[];
+  u32 (*s_map)[kLinkSmem / 2] = reinterpret_cast<u32 (*)[kLinkSmem / 2]>(link_smem);
+  u32 (*s_list)[kLinkSmem] =
+      reinterpret_cast<u32 (*)[kLinkSmem]>(link_smem + (size_t)kLinkWarps * (kLinkSmem / 2));
   __shared__ u32 s_pref[kLinkWarps][33];
-  __shared__ u32 s_sb[kLinkWarps][32];
+  __shared__ u64 s_start[kLinkWarps][32];
+  __shared__ u32 s_cnt[kLinkWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 gw = blockIdx.x * kLinkWarps + wid;
   const u32 nwarps = gridDim.x * kLinkWarps;
-  u32* gmap = scratch + (u64)gw * dmax;
+  u32* gmap = scratch + (u64)gw * 2 * dmax;
+  u32* glist = gmap + dmax;
   for (u32 i = lane; i < kLinkSmem / 2; i += 32) s_map[wid][i] = 0;
   __syncwarp();
   for (u64 s = gw; s < g.S; s += nwarps) {
@@ -510,69 +520,79 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
     }
     const u32 ub = g.rowptr[lo], du = g.rowptr[lo + 1] - ub;
     const bool small = du <= kLinkSmem;
+    u32* list = small ? s_list[wid] : glist;
+    if (lane == 0) s_cnt[wid] = 0;
+    __syncwarp();
     u64 c4 = 0;
-    u32 steps = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-      if (pass == 1) {
-        // clear: in bulk when cheaper than walking the lists again
-        if (small && steps >= du / 2) {
-          for (u32 i = lane; i < (du + 1) / 2; i += 32) s_map[wid][i] = 0;
-          break;
+    for (u64 k0 = g.tl_ptr[s]; k0 < g.tl_ptr[s + 1]; k0 += 32) {
+      const u64 k = k0 + lane;
+      u32 len = 0;
+      u64 st0 = 0;
+      if (k < g.tl_ptr[s + 1]) {
+        const u32 sb = g.tl[k];
+        u64 l2 = g.tl_ptr[sb], h2 = g.tl_ptr[sb + 1];
+        const u64 end = h2;
+        while (l2 < h2) {  // first partner slot > s
+          const u64 mid = l2 + ((h2 - l2) >> 1);
+          if (g.tl[mid] <= (u32)s) l2 = mid + 1;
+          else h2 = mid;
         }
-        if (!small && steps >= du) {
-          for (u32 i = lane; i < du; i += 32) gmap[i] = 0;
-          break;
-        }
+        st0 = l2;
+        len = (u32)(end - l2);
       }
-      for (u64 k0 = g.tl_ptr[s]; k0 < g.tl_ptr[s + 1]; k0 += 32) {
-        const u64 k = k0 + lane;
-        u32 sb = 0, len = 0;
-        if (k < g.tl_ptr[s + 1]) {
-          sb = g.tl[k];
-          len = sa.T[sb];
-        }
-        u32 incl = len;
+      u32 incl = len;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        s_pref[wid][lane + 1] = incl;
-        if (lane == 0) s_pref[wid][0] = 0;
-        s_sb[wid][lane] = sb;
-        __syncwarp();
-        const u32 tot = s_pref[wid][32];
-        for (u32 it = lane; it < tot; it += 32) {
-          u32 l2 = 0, h2 = 32;
-          while (h2 - l2 > 1) {
-            const u32 mid = (l2 + h2) >> 1;
-            if (s_pref[wid][mid] <= it) l2 = mid;
-            else h2 = mid;
-          }
-          const u32 sbb = s_sb[wid][l2];
-          const u32 sc = g.tl[g.tl_ptr[sbb] + (it - s_pref[wid][l2])];
-          if (sc == (u32)s) continue;
-          const u32 pc = sc - ub;
-          if (pass == 0) {
-            if (small) {
-              const u32 sh = (pc & 1u) * 16u;
-              c4 += (atomicAdd(&s_map[wid][pc >> 1], 1u << sh) >> sh) & 0xffffu;
-            } else {
-              c4 += atomicAdd(&gmap[pc], 1u);
-            }
-            ++steps;
-          } else {
-            if (small) s_map[wid][pc >> 1] = 0;
-            else gmap[pc] = 0;
-          }
-        }
-        __syncwarp();
+      for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      if (pass == 0) steps = (u32)warp_sum(steps);
+      s_pref[wid][lane + 1] = incl;
+      if (lane == 0) s_pref[wid][0] = 0;
+      s_start[wid][lane] = st0;
+      __syncwarp();
+      const u32 tot = s_pref[wid][32];
+      for (u32 it = lane; it < tot; it += 32) {
+        u32 l2 = 0, h2 = 32;
+        while (h2 - l2 > 1) {
+          const u32 mid = (l2 + h2) >> 1;
+          if (s_pref[wid][mid] <= it) l2 = mid;
+          else h2 = mid;
+        }
+        const u32 pc = g.tl[s_start[wid][l2] + (it - s_pref[wid][l2])] - ub;
+        u32 old;
+        if (small) {
+          const u32 sh = (pc & 1u) * 16u;
+          old = (atomicAdd(&s_map[wid][pc >> 1], 1u << sh) >> sh) & 0xffffu;
+        } else {
+          old = atomicAdd(&gmap[pc], 1u);
+        }
+        c4 += old;
+        if (old == 0) list[atomicAdd(&s_cnt[wid], 1u)] = pc;
+      }
+      __syncwarp();
+    }
+    // credit each partner c > a with C(W_ac, 2) and clear its counter
+    const u32 cnt = s_cnt[wid];
+    for (u32 i = lane; i < cnt; i += 32) {
+      const u32 pc = list[i];
+      u32 w;
+      if (small) {
+        const u32 sh = (pc & 1u) * 16u;
+        w = (s_map[wid][pc >> 1] >> sh) & 0xffffu;
+      } else {
+        w = gmap[pc];
+      }
+      if (w >= 2) atomicAdd(&sa.b68[ub + pc], (u64)w * (w - 1) / 2);
+    }
+    __syncwarp();
+    for (u32 i = lane; i < cnt; i += 32) {
+      const u32 pc = list[i];
+      if (small) s_map[wid][pc >> 1] = 0;
+      else gmap[pc] = 0;
     }
     __syncwarp();
     c4 = warp_sum(c4);
-    if (lane == 0) sa.b68[s] = c4;
+    if (lane == 0 && c4) atomicAdd(&sa.b68[s], c4);
   }
 }
 
@@ -626,8 +646,9 @@ k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
   extern __shared__ u32 k5_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 words = (smax + 31) / 32;
-  u32* S = k5_smem + (size_t)wid * (smax + (size_t)smax * words);
-  u32* rows = S + smax;
+  u32* S = k5_smem + (size_t)wid * (2 * smax + (size_t)smax * words);
+  u32* tcnt = S + smax;
+  u32* rows = tcnt + smax;
   const u32 n = g.n;
   const u32 gw = blockIdx.x * kK5Warps + wid;
   const u32 nw = gridDim.x * kK5Warps;
@@ -681,19 +702,35 @@ k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
       }
     }
     __syncwarp();
-    u64 tot = 0;
+    // per unordered edge (c,d) of G[S], c < d: k_cd = |N_S(c) ^ N_S(d)|
+    // triangles; crediting k_cd to both ends gives each vertex twice its
+    // triangle count
+    for (u32 ci = lane; ci < s; ci += 32) tcnt[ci] = 0;
+    __syncwarp();
     for (u32 ci = lane; ci < s; ci += 32) {
       const u32* rc = rows + ci * w;
-      u32 t2 = 0;
-      for (u32 k = 0; k < w; ++k) {
+      u32 tc = 0;
+      for (u32 k = (ci + 1) >> 5; k < w; ++k) {
         u32 bits = rc[k];
+        if (k == (ci >> 5)) bits &= ~((2u << (ci & 31)) - 1u);  // partners d > c
         while (bits) {
           const u32 di = k * 32 + __ffs(bits) - 1;
           bits &= bits - 1;
           const u32* rd = rows + di * w;
-          for (u32 q = 0; q < w; ++q) t2 += __popc(rc[q] & rd[q]);
+          u32 kcd = 0;
+          for (u32 q = 0; q < w; ++q) kcd += __popc(rc[q] & rd[q]);
+          if (kcd) {
+            tc += kcd;
+            atomicAdd(&tcnt[di], kcd);
+          }
         }
       }
+      if (tc) atomicAdd(&tcnt[ci], tc);
+    }
+    __syncwarp();
+    u64 tot = 0;
+    for (u32 ci = lane; ci < s; ci += 32) {
+      const u32 t2 = tcnt[ci];
       const u32 tc = t2 >> 1;
       if (tc) atomicAdd(&acc[(u64)A_K5 * n + S[ci]], (u64)tc);
       tot += tc;
@@ -732,10 +769,14 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
     root_kernel<512><<<rs.ctas, 512, 0, st>>>(g, sa, acc, rs, pref, pref_stride);
 }
 
+void link_configure() {
+  cudaFuncSetAttribute(link_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinkDynSmem);
+}
+
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
                  cudaStream_t st) {
   if (!g.S || !warps) return;
-  link_kernel<<<warps / kLinkWarps, kLinkWarps * 32, 0, st>>>(g, sa, scratch, dmax);
+  link_kernel<<<warps / kLinkWarps, kLinkWarps * 32, kLinkDynSmem, st>>>(g, sa, scratch, dmax);
 }
 
 K5Config k5_configure(u32 max_outdeg) {
@@ -745,7 +786,7 @@ K5Config k5_configure(u32 max_outdeg) {
   u32 smax = (max_outdeg + 31) / 32 * 32;
   const u32 cap = 640;
   if (smax > cap) smax = cap;
-  const size_t per_warp = ((size_t)smax + (size_t)smax * ((smax + 31) / 32)) * sizeof(u32);
+  const size_t per_warp = (2 * (size_t)smax + (size_t)smax * ((smax + 31) / 32)) * sizeof(u32);
   c.smem = per_warp * kK5Warps;
   c.smax = smax;
   cudaFuncSetAttribute(k5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
