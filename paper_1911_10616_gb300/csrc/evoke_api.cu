@@ -418,7 +418,7 @@ int plan_stage1(evoke_plan* P, bool validate) {
   const u64 m = P->m, S = 2 * m;
   size_t bytes = sz<u32>(n) + sz<u32>(S) + sz<u32>(n + 1) + 2 * sz<u32>(m) + sz<u32>(n) +
                  sz<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1)) + sz<u32>(S) +
-                 sz<u64>(S + 1) + sz<int>(4) + sz<u32>(4);
+                 sz<u64>(S + 1) + sz<int>(4) + sz<u32>(4) + sz<unsigned char>(S);
   if (P->batch) bytes += sz<u32>(n + 1) + sz<u32>(S) + sz<u32>(n);
   if (cudaMallocAsync(&P->block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   P->bytes = bytes;
@@ -437,6 +437,7 @@ int plan_stage1(evoke_plan* P, bool validate) {
   g.col = P->col;
   g.deg = ar.take<u32>(n);
   g.rev = ar.take<u32>(S);
+  g.sin = ar.take<unsigned char>(S);
   g.dag_ptr = ar.take<u32>(n + 1);
   g.dag_col = ar.take<u32>(m);
   g.dag_slot = ar.take<u32>(m);

@@ -100,6 +100,7 @@ struct Graph {
   const u32* col;        // S
   u32* deg;              // n
   u32* rev;              // S: slot of (v,u) for slot (u,v)
+  unsigned char* sin;    // S: 1 if slot (u,v) is an in-edge of u in the DAG (v precedes u)
   u32* dag_ptr;          // n+1: out-neighbours (u -> v iff u precedes v)
   u32* dag_col;          // m
   u32* dag_slot;         // m: CSR slot of each DAG edge (in the source row)

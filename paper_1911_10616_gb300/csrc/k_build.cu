@@ -43,13 +43,18 @@ __global__ void rev_kernel(const u32* __restrict__ rowptr, const u32* __restrict
 }
 
 __global__ void dag_count_kernel(const u32* __restrict__ rowptr, const u32* __restrict__ col,
-                                 const u32* __restrict__ deg, u32* __restrict__ cnt, u32 n) {
+                                 const u32* __restrict__ deg, u32* __restrict__ cnt,
+                                 unsigned char* __restrict__ sin, u32 n) {
   const u32 warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
   const u32 u = warp;
   u32 c = 0;
-  for (u32 s = rowptr[u] + lane; s < rowptr[u + 1]; s += 32) c += prec(deg, u, col[s]) ? 1u : 0u;
+  for (u32 s = rowptr[u] + lane; s < rowptr[u + 1]; s += 32) {
+    const bool out = prec(deg, u, col[s]);
+    c += out ? 1u : 0u;
+    if (sin) sin[s] = out ? 0 : 1;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if (lane == 0) cnt[u] = c;
@@ -269,7 +274,8 @@ void launch_dag(const Graph& g, u32* cnt, void* scan_tmp, cudaStream_t st) {
   }
   const u64 threads = (u64)g.n * 32;
   const unsigned blocks = (unsigned)((threads + kWarpsPerBlock * 32 - 1) / (kWarpsPerBlock * 32));
-  dag_count_kernel<<<blocks, kWarpsPerBlock * 32, 0, st>>>(g.rowptr, g.col, g.deg, cnt, g.n);
+  dag_count_kernel<<<blocks, kWarpsPerBlock * 32, 0, st>>>(g.rowptr, g.col, g.deg, cnt, g.sin,
+                                                           g.n);
   cudaMemcpyAsync(g.dag_ptr, cnt, sizeof(u32) * g.n, cudaMemcpyDeviceToDevice, st);
   launch_scan_u32_inplace(g.dag_ptr, g.n, scan_tmp, st);
   dag_fill_kernel<<<blocks, kWarpsPerBlock * 32, 0, st>>>(g.rowptr, g.col, g.deg, g.dag_ptr,

@@ -143,6 +143,8 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
   __shared__ u32 s_wsa[kThreads / 32][32];
   __shared__ u32 s_wsb[kThreads / 32][32];
   __shared__ u32 s_pref[kSmemPref + 1];
+  __shared__ u32 s_nrp[kSmemPref];            // rowptr of each neighbour (small roots)
+  __shared__ unsigned char s_nout[kSmemPref];  // u -> neighbour in the DAG
   __shared__ u32 s_root, s_nt, s_nj, s_carry;
   __shared__ u64 s_red[32];
   __shared__ long long s_t0;
@@ -181,18 +183,37 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       H[v - cb].W = kFlag;
       touched[atomicAdd(&s_nt, 1u)] = v;
     }
+    const bool small = du + 1 <= kSmemPref;
+    if (small)
+      for (u32 i = threadIdx.x; i < du; i += blockDim.x) {
+        const u32 v = g.col[ub + i];
+        s_nrp[i] = g.rowptr[v];
+        s_nout[i] = prec(g.deg, u, v) ? 1 : 0;
+      }
     neighbour_degree_prefix(g, ub, du, pref, s_red, &s_carry);
     const u32 total = pref[du];
+    // wedge w = (u, v_i, x): neighbour index i, slot t of x in row v_i, u -> v_i
+    auto wedge = [&](u32 w, u32& i, u32& t, bool& out) {
+      i = seg_find(pref, du + 1, w);
+      if (small) {
+        t = s_nrp[i] + (w - pref[i]);
+        out = s_nout[i] != 0;
+      } else {
+        const u32 v = g.col[ub + i];
+        t = g.rowptr[v] + (w - pref[i]);
+        out = prec(g.deg, u, v);
+      }
+    };
 
     // phase 1: wedges u - v - x.  W (low word) and Wn (high word) of the hot
     // record are bumped by one 64-bit atomic.
     for (u32 w = threadIdx.x; w < total; w += blockDim.x) {
-      const u32 i = seg_find(pref, du + 1, w);
-      const u32 v = g.col[ub + i];
-      const u32 t = g.rowptr[v] + (w - pref[i]);
+      u32 i, t;
+      bool out;
+      wedge(w, i, t, out);
       const u32 x = g.col[t];
       if (x == u) continue;
-      const bool in_in = prec(g.deg, u, v) && prec(g.deg, x, v);
+      const bool in_in = out && g.sin[t];  // u -> v <- x
       const u64 old = atomicAdd(reinterpret_cast<u64*>(&H[x - cb].W),
                                 in_in ? 1ull : (1ull | (1ull << 32)));
       if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
@@ -349,9 +370,9 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         u32 s = 0;
         u64 e5 = 0, b49 = 0, b62 = 0, bw = 0;
         if (valid) {
-          const u32 i = seg_find(pref, du + 1, w);
-          const u32 v = g.col[ub + i];
-          const u32 t = g.rowptr[v] + (w - pref[i]);
+          u32 i, t;
+          bool out;
+          wedge(w, i, t, out);
           const u32 x = g.col[t];
           s = ub + i;
           if (x == u) {
@@ -365,7 +386,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
               b49 = c2(wx - 1);
               b62 = h.D;
             }
-            if (!(prec(g.deg, u, v) && prec(g.deg, x, v))) bw = h.P;
+            if (!(out && g.sin[t])) bw = h.P;
           }
         }
         seg_atomic_add(sa.E5, s, valid, e5);
