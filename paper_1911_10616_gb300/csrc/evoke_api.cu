@@ -303,6 +303,32 @@ __global__ void dmax_kernel(const u32* deg, const u32* dag_ptr, u32 n, u32* out)
   }
 }
 
+__global__ void degree_max_kernel(const u32* rowptr, u32 n, u32* out) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  u32 v = u < n ? rowptr[u + 1] - rowptr[u] : 0;
+  const u32 l = (u < n && v > 1024u) ? 1u : 0u;
+  u32 c = l;
+  for (int o = 16; o > 0; o >>= 1) {
+    v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (v) atomicMax(out, v);
+    if (c) atomicAdd(out + 1, c);
+  }
+}
+template <typename T>
+__global__ void unpermute_rows_kernel(const T* in, T* out, const u32* old_of, u32 n, u32 width) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (u64)n * width) return;
+  const u32 r = (u32)(i / width), k = (u32)(i % width);
+  out[(u64)old_of[r] * width + k] = in[i];
+}
+__global__ void unpermute_slots_kernel(const long long* in, long long* out, const u32* orig, u64 S) {
+  const u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < S) out[orig[s]] = in[s];
+}
+
 __global__ void widen_kernel(const u32* in, long long* out, u64 count) {
   u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) out[i] = in[i];
@@ -366,6 +392,19 @@ struct evoke_plan {
   u32* union_rowptr = nullptr;
   u32* union_col = nullptr;
   u32* comp_base = nullptr;
+  // relabelling by decreasing degree (single graphs): the passes run on the
+  // relabelled CSR; outputs are mapped back to the caller's ids
+  bool relabel = false;
+  const u32* in_rowptr = nullptr;
+  const u32* in_col = nullptr;
+  u32* rl_new_id = nullptr;
+  u32* rl_old_of = nullptr;
+  u32* rl_rowptr = nullptr;
+  u32* rl_col = nullptr;
+  u32* rl_hist = nullptr;
+  u32 rl_dmax = 0;
+  u32 rl_long_rows = 0;
+  void* rl_block = nullptr;
   cudaStream_t st = nullptr;
   int launches_per_exec = 0;
   int ctas_alloc = 0;     // CTAs the root maps were allocated for
@@ -411,6 +450,79 @@ void apply_config(evoke_plan* P, u32 map_n) {
   if ((size_t)sms * 4 * per_cta <= budget) P->ctas_alloc = std::max(P->ctas_alloc, sms * 4);
 }
 
+// the CSR invariants of the caller's graph (simple, symmetric, sorted rows)
+int validate_csr(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
+                 cudaStream_t st) {
+  if (!n) return EVOKE_OK;
+  const u64 S = 2 * m;
+  size_t bytes = sz<u32>(S) + sz<int>(4);
+  void* blk = nullptr;
+  if (cudaMallocAsync(&blk, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  Graph g{};
+  g.n = n;
+  g.S = S;
+  g.rowptr = rowptr;
+  g.col = colidx;
+  g.rev = static_cast<u32*>(blk);
+  int* status = reinterpret_cast<int*>(static_cast<char*>(blk) + sz<u32>(S));
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  launch_rev_validate(g, status, st);
+  int h = 0;
+  cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(blk, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
+  if (h & ST_RANGE) return EVOKE_ERANGE;
+  if (h & ST_NOT_SIMPLE) return EVOKE_ENOTSIMPLE;
+  return EVOKE_OK;
+}
+
+bool relabel_wanted() {
+  const char* e = getenv("EVOKE_NO_RELABEL");
+  return !(e && *e && *e != '0');
+}
+
+void relabel_run(evoke_plan* P, cudaStream_t st) {
+  relabel_prepare(P->in_rowptr, P->n, P->rl_dmax, P->rl_hist, P->rl_new_id, P->rl_old_of,
+                  P->rl_rowptr, st);
+  launch_scan_u32_inplace(P->rl_rowptr, P->n, P->scan_tmp, st);
+  relabel_build(P->in_rowptr, P->in_col, P->rl_new_id, P->rl_old_of, P->rl_rowptr, P->rl_col, P->n,
+                P->rl_long_rows, P->rl_dmax, st);
+}
+
+// decide on relabelling and allocate its buffers (single graphs)
+int plan_relabel_setup(evoke_plan* P) {
+  if (P->batch || !relabel_wanted() || P->n < 2) return EVOKE_OK;
+  cudaStream_t st = P->st;
+  u32* d = nullptr;
+  if (cudaMallocAsync(&d, 2 * sizeof(u32), st) != cudaSuccess) return EVOKE_ENOMEM;
+  cudaMemsetAsync(d, 0, 2 * sizeof(u32), st);
+  degree_max_kernel<<<(P->n + 255) / 256, 256, 0, st>>>(P->rowptr, P->n, d);
+  u32 h[2] = {0, 0};
+  cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
+  if (h[0] > kRelabelMaxDegree) return EVOKE_OK;  // rows too long for the in-place sort
+  const u64 S = 2 * P->m;
+  size_t bytes = 3 * sz<u32>(P->n + 1) + sz<u32>(S) + sz<u32>(h[0] + 1);
+  if (cudaMallocAsync(&P->rl_block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  Arena ar{static_cast<char*>(P->rl_block), bytes, 0, st};
+  P->rl_new_id = ar.take<u32>(P->n + 1);
+  P->rl_old_of = ar.take<u32>(P->n + 1);
+  P->rl_rowptr = ar.take<u32>(P->n + 1);
+  P->rl_col = ar.take<u32>(S);
+  P->rl_hist = ar.take<u32>(h[0] + 1);
+  if (ar.overflow) return EVOKE_ENOMEM;
+  P->rl_dmax = h[0];
+  P->rl_long_rows = h[1];
+  relabel_configure(h[0]);
+  P->in_rowptr = P->rowptr;
+  P->in_col = P->col;
+  P->rowptr = P->rl_rowptr;
+  P->col = P->rl_col;
+  P->relabel = true;
+  return EVOKE_OK;
+}
+
 // stage 1 buffers (graph-sized) and the sizing passes
 int plan_stage1(evoke_plan* P, bool validate) {
   cudaStream_t st = P->st;
@@ -453,6 +565,7 @@ int plan_stage1(evoke_plan* P, bool validate) {
   if (P->batch)
     launch_union_csr(P->rowptr_cat, P->col_cat, P->vtx_off, P->edge_off, P->G, n, S,
                      P->union_rowptr, P->union_col, P->comp_base, st);
+  if (P->relabel) relabel_run(P, st);
   launch_degrees(g, st);
   launch_rev_validate(g, P->status, st);
   if (validate) {
@@ -570,6 +683,10 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
       launch_union_csr(P->rowptr_cat, P->col_cat, P->vtx_off, P->edge_off, P->G, n, S,
                        P->union_rowptr, P->union_col, P->comp_base, st);
     });
+  if (P->relabel)
+    run("relabel", 6 + (P->rl_long_rows ? 1 : 0) + (n > P->rl_long_rows ? 1 : 0), [&] {
+      relabel_run(P, st);
+    });
   run("degrees", nl, [&] { launch_degrees(g, st); });
   run("rev", nl, [&] { launch_rev_validate(g, P->status, st); });
   run("dag", n ? 5 : 0, [&] { launch_dag(g, P->cnt, P->scan_tmp, st); });
@@ -599,13 +716,15 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
   run("tri_opp2", nl, [&] { launch_tri_opp2(g, sa, acc, st); });
   run("vsum2", nl, [&] { launch_vsum2(g, sa, acc, st); });
   run("vsum3", nl, [&] { launch_vsum3(g, acc, st); });
-  if (out) run("finalize", nl, [&] { launch_finalize(g, acc, out, st); });
+  if (out)
+    run("finalize", nl, [&] { launch_finalize(g, acc, out, P->relabel ? P->rl_old_of : nullptr, st); });
 }
 
 int count_launches(const evoke_plan* P, bool with_out) {
   const int nl = P->n ? 1 : 0, sl = P->g.S ? 1 : 0;
   int k = 0;
   if (P->batch) k += 1 + sl;
+  if (P->relabel) k += 6 + (P->rl_long_rows ? 1 : 0) + (P->n > P->rl_long_rows ? 1 : 0);
   k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + sl + nl + nl;
   k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl + sl + (P->k5.blocks ? 1 : 0) + nl + nl + nl;
   if (P->model) k += 2 * nl;
@@ -617,6 +736,7 @@ void plan_free(evoke_plan* P) {
   if (!P) return;
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->model_block) cudaFreeAsync(P->model_block, P->st);
+  if (P->rl_block) cudaFreeAsync(P->rl_block, P->st);
   if (P->block) cudaFreeAsync(P->block, P->st);
   if (P->block2) cudaFreeAsync(P->block2, P->st);
   cudaStreamSynchronize(P->st);
@@ -646,7 +766,15 @@ int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, ui
   P->m = m;
   P->st = st;
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
-  rc = plan_stage1(P, opts && opts->validate);
+  if (opts && opts->validate) {  // validate the caller's CSR before relabelling it
+    rc = validate_csr(rowptr, colidx, n, m, st);
+    if (rc) {
+      plan_free(P);
+      return rc;
+    }
+  }
+  rc = plan_relabel_setup(P);
+  if (!rc) rc = plan_stage1(P, false);
   if (!rc) rc = plan_stage2(P);
   if (rc) {
     plan_free(P);
@@ -908,7 +1036,18 @@ int evoke_plan_set_model(evoke_plan* plan, const float* params) {
 
 int evoke_plan_features(evoke_plan* plan, float* X, void* stream) {
   if (!plan || (plan->n && !X)) return EVOKE_EINVAL;
-  launch_features(plan->g, plan->acc, X, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!plan->relabel) {
+    launch_features(plan->g, plan->acc, X, st);
+  } else if (plan->n) {
+    float* tmp = nullptr;
+    if (cudaMallocAsync(&tmp, sizeof(float) * 4 * (size_t)plan->n, st) != cudaSuccess) return EVOKE_ENOMEM;
+    launch_features(plan->g, plan->acc, tmp, st);
+    const u64 cnt = 4 * (u64)plan->n;
+    unpermute_rows_kernel<float><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
+        tmp, X, plan->rl_old_of, plan->n, 4);
+    cudaFreeAsync(tmp, st);
+  }
   return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
 }
 
@@ -916,11 +1055,20 @@ int evoke_plan_root_timing(evoke_plan* plan, uint64_t* root_cycles, uint64_t* ct
                            int64_t* out, void* stream) {
   if (!plan) return EVOKE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  plan->rs.cycles = reinterpret_cast<u64*>(root_cycles);
+  u64* cyc = reinterpret_cast<u64*>(root_cycles);
+  if (root_cycles && plan->relabel && plan->n &&
+      cudaMallocAsync(&cyc, sizeof(u64) * (size_t)plan->n, st) != cudaSuccess)
+    return EVOKE_ENOMEM;
+  plan->rs.cycles = cyc;
   plan->rs.cta_end = reinterpret_cast<u64*>(cta_end_ns);
   execute(plan, reinterpret_cast<long long*>(out), st, /*timed=*/false);
   plan->rs.cycles = nullptr;
   plan->rs.cta_end = nullptr;
+  if (root_cycles && plan->relabel && plan->n) {
+    unpermute_rows_kernel<u64><<<(plan->n + 255) / 256, 256, 0, st>>>(
+        cyc, reinterpret_cast<u64*>(root_cycles), plan->rl_old_of, plan->n, 1);
+    cudaFreeAsync(cyc, st);
+  }
   {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_launches += (unsigned long long)count_launches(plan, out != nullptr);
@@ -1025,11 +1173,34 @@ int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n
   const u64 S = P->g.S;
   const unsigned eb = (unsigned)((S + 255) / 256);
   if (!rc && S) {
-    if (tri) widen_kernel<<<eb, 256, 0, st>>>(P->sa.T, reinterpret_cast<long long*>(tri), S);
-    if (c4) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E5, reinterpret_cast<long long*>(c4), S);
-    if (k4) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.K4, reinterpret_cast<long long*>(k4), S);
-    if (e7) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E7, reinterpret_cast<long long*>(e7), S);
-    if (e9) copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E9, reinterpret_cast<long long*>(e9), S);
+    // per-slot values in the plan's slot order, then (relabelled plans) in the caller's
+    long long* tmp = nullptr;
+    u32* orig = nullptr;
+    if (P->relabel) {
+      if (cudaMallocAsync(&tmp, sizeof(long long) * S, st) != cudaSuccess ||
+          cudaMallocAsync(&orig, sizeof(u32) * S, st) != cudaSuccess)
+        rc = EVOKE_ENOMEM;
+      else
+        launch_orig_slot(P->in_rowptr, P->in_col, P->rl_old_of, P->rl_rowptr, P->rl_col, P->n,
+                         orig, st);
+    }
+    auto emit = [&](auto&& fill, int64_t* dst) {
+      if (!dst || rc) return;
+      long long* d = reinterpret_cast<long long*>(dst);
+      if (!P->relabel) {
+        fill(d);
+      } else {
+        fill(tmp);
+        unpermute_slots_kernel<<<eb, 256, 0, st>>>(tmp, d, orig, S);
+      }
+    };
+    emit([&](long long* d) { widen_kernel<<<eb, 256, 0, st>>>(P->sa.T, d, S); }, tri);
+    emit([&](long long* d) { copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E5, d, S); }, c4);
+    emit([&](long long* d) { copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.K4, d, S); }, k4);
+    emit([&](long long* d) { copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E7, d, S); }, e7);
+    emit([&](long long* d) { copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E9, d, S); }, e9);
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (orig) cudaFreeAsync(orig, st);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = EVOKE_ECUDA;
   }
   plan_free(P);

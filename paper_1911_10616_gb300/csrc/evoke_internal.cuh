@@ -233,12 +233,22 @@ void launch_k4_known(const Graph& g, const SlotArrays& sa, u64* acc, u64 total, 
 void launch_union_csr(const u32* rowptr_cat, const u32* col_cat, const long long* vtx_off,
                       const long long* edge_off, u32 G, u32 n, u64 S, u32* rowptr, u32* col,
                       u32* comp_base, cudaStream_t st);
+// relabelling by decreasing degree (single graphs)
+constexpr u32 kRelabelMaxDegree = 32768;  // longest row the block sort holds in shared memory
+u32 relabel_prepare(const u32* rowptr, u32 n, u32 dmax, u32* hist, u32* new_id, u32* old_of,
+                    u32* new_deg, cudaStream_t st);
+void relabel_build(const u32* rowptr, const u32* col, const u32* new_id, const u32* old_of,
+                   const u32* nrow, u32* ncol, u32 n, u32 long_rows, u32 dmax, cudaStream_t st);
+void relabel_configure(u32 dmax);
+void launch_orig_slot(const u32* rowptr, const u32* col, const u32* old_of, const u32* nrow,
+                      const u32* ncol, u32 n, u32* orig, cudaStream_t st);
 void launch_max_component(const long long* vtx_off, u32 G, u32* out, cudaStream_t st);
 void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);
 int upload_transform(const long long* A73x73);
-void launch_finalize(const Graph& g, const u64* acc, long long* out, cudaStream_t st);
+void launch_finalize(const Graph& g, const u64* acc, long long* out, const u32* old_of,
+                     cudaStream_t st);
 // learned work model
 int mlp_param_count();
 void launch_features(const Graph& g, const u64* acc, float* X, cudaStream_t st);

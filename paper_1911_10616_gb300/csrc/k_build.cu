@@ -209,7 +209,160 @@ __global__ void max_component_kernel(const long long* vtx_off, u32 G, u32* out) 
   if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
 }
 
+// ---- relabelling by decreasing degree ---------------------------------------
+// Vertices are renumbered so that ids ascend as degrees descend; hubs, whose
+// 2-hop-map entries every root touches most, then share a small id range.
+__global__ void deg_hist_kernel(const u32* __restrict__ rowptr, u32 n, u32* hist) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n) atomicAdd(&hist[rowptr[u + 1] - rowptr[u]], 1u);
+}
+// exclusive prefix over degrees from the largest down (one block)
+__global__ void deg_scan_desc_kernel(u32* hist, u32 dmax) {
+  __shared__ u32 carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (u32 b0 = 0; b0 <= dmax; b0 += blockDim.x) {
+    const u32 i = b0 + threadIdx.x;  // i-th largest degree
+    const u32 dgr = i <= dmax ? dmax - i : 0;
+    const u32 v = i <= dmax ? hist[dgr] : 0;
+    // block inclusive scan
+    __shared__ u32 tmp[1024];
+    tmp[threadIdx.x] = v;
+    __syncthreads();
+    for (u32 o = 1; o < blockDim.x; o <<= 1) {
+      const u32 y = threadIdx.x >= o ? tmp[threadIdx.x - o] : 0;
+      __syncthreads();
+      tmp[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i <= dmax) hist[dgr] = carry + tmp[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += tmp[threadIdx.x];
+    __syncthreads();
+  }
+}
+__global__ void relabel_scatter_kernel(const u32* __restrict__ rowptr, u32 n, u32* cursor,
+                                       u32* __restrict__ new_id, u32* __restrict__ old_of,
+                                       u32* __restrict__ new_deg) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const u32 d = rowptr[u + 1] - rowptr[u];
+  const u32 k = atomicAdd(&cursor[d], 1u);
+  new_id[u] = k;
+  old_of[k] = u;
+  new_deg[k] = d;
+}
+// rows of the relabelled graph, unsorted: warp per new row
+__global__ void relabel_fill_kernel(const u32* __restrict__ rowptr, const u32* __restrict__ col,
+                                    const u32* __restrict__ new_id, const u32* __restrict__ old_of,
+                                    const u32* __restrict__ nrow, u32* __restrict__ ncol, u32 n) {
+  const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const u32 u = old_of[w];
+  const u32 b = rowptr[u], d = rowptr[u + 1] - b, o = nrow[w];
+  for (u32 k = lane; k < d; k += 32) ncol[o + k] = new_id[col[b + k]];
+}
+// bitonic sort of one row in shared memory (ascending, padded with ~0)
+template <bool kBlock>
+__device__ void bitonic_sort(u32* a, u32 len, u32 tid, u32 nthreads) {
+  for (u32 k = 2; k <= len; k <<= 1)
+    for (u32 j = k >> 1; j > 0; j >>= 1) {
+      for (u32 i = tid; i < len; i += nthreads) {
+        const u32 ixj = i ^ j;
+        if (ixj > i) {
+          const u32 x = a[i], y = a[ixj];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      if (kBlock) __syncthreads();
+      else __syncwarp();
+    }
+}
+constexpr u32 kWarpSortMax = 1024;
+__global__ void row_sort_warp_kernel(const u32* __restrict__ nrow, u32* ncol, u32 first, u32 n) {
+  __shared__ u32 buf[8][kWarpSortMax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 r = first + blockIdx.x * 8 + wid;
+  if (r >= n) return;
+  const u32 b = nrow[r], d = nrow[r + 1] - b;
+  if (d < 2) return;
+  u32 len = 1;
+  while (len < d) len <<= 1;
+  for (u32 k = lane; k < len; k += 32) buf[wid][k] = k < d ? ncol[b + k] : 0xffffffffu;
+  __syncwarp();
+  bitonic_sort<false>(buf[wid], len, lane, 32);
+  for (u32 k = lane; k < d; k += 32) ncol[b + k] = buf[wid][k];
+}
+__global__ void row_sort_block_kernel(const u32* __restrict__ nrow, u32* ncol) {
+  extern __shared__ u32 big[];
+  const u32 r = blockIdx.x;
+  const u32 b = nrow[r], d = nrow[r + 1] - b;
+  u32 len = 1;
+  while (len < d) len <<= 1;
+  for (u32 k = threadIdx.x; k < len; k += blockDim.x) big[k] = k < d ? ncol[b + k] : 0xffffffffu;
+  __syncthreads();
+  bitonic_sort<true>(big, len, threadIdx.x, blockDim.x);
+  for (u32 k = threadIdx.x; k < d; k += blockDim.x) ncol[b + k] = big[k];
+}
+// original slot of every relabelled slot (for per-edge outputs)
+__global__ void orig_slot_kernel(const u32* __restrict__ rowptr, const u32* __restrict__ col,
+                                 const u32* __restrict__ old_of, const u32* __restrict__ nrow,
+                                 const u32* __restrict__ ncol, u32 n, u32* __restrict__ orig) {
+  const u32 w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const u32 u = old_of[w];
+  const u32 b = rowptr[u], e = rowptr[u + 1];
+  for (u32 s = nrow[w] + lane; s < nrow[w + 1]; s += 32) {
+    const u32 v = old_of[ncol[s]];
+    orig[s] = lower_bound_u32(col, b, e, v);
+  }
+}
+
 }  // namespace
+
+u32 relabel_prepare(const u32* rowptr, u32 n, u32 dmax, u32* hist, u32* new_id, u32* old_of,
+                    u32* new_deg, cudaStream_t st) {
+  // returns nothing on the host side; the number of long rows is derived later
+  cudaMemsetAsync(hist, 0, sizeof(u32) * (dmax + 1), st);
+  deg_hist_kernel<<<(n + 255) / 256, 256, 0, st>>>(rowptr, n, hist);
+  deg_scan_desc_kernel<<<1, 1024, 0, st>>>(hist, dmax);
+  relabel_scatter_kernel<<<(n + 255) / 256, 256, 0, st>>>(rowptr, n, hist, new_id, old_of, new_deg);
+  return 0;
+}
+
+void relabel_build(const u32* rowptr, const u32* col, const u32* new_id, const u32* old_of,
+                   const u32* nrow, u32* ncol, u32 n, u32 long_rows, u32 dmax, cudaStream_t st) {
+  if (!n) return;
+  relabel_fill_kernel<<<(unsigned)(((u64)n * 32 + 255) / 256), 256, 0, st>>>(rowptr, col, new_id,
+                                                                             old_of, nrow, ncol, n);
+  if (long_rows) {
+    u32 len = 1;
+    while (len < dmax) len <<= 1;
+    row_sort_block_kernel<<<long_rows, 1024, len * sizeof(u32), st>>>(nrow, ncol);
+  }
+  if (n > long_rows)
+    row_sort_warp_kernel<<<(n - long_rows + 7) / 8, 256, 0, st>>>(nrow, ncol, long_rows, n);
+}
+
+void relabel_configure(u32 dmax) {
+  u32 len = 1;
+  while (len < dmax) len <<= 1;
+  cudaFuncSetAttribute(row_sort_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(len * sizeof(u32)));
+}
+
+void launch_orig_slot(const u32* rowptr, const u32* col, const u32* old_of, const u32* nrow,
+                      const u32* ncol, u32 n, u32* orig, cudaStream_t st) {
+  if (n)
+    orig_slot_kernel<<<(unsigned)(((u64)n * 32 + 255) / 256), 256, 0, st>>>(rowptr, col, old_of,
+                                                                           nrow, ncol, n, orig);
+}
 
 void launch_union_csr(const u32* rowptr_cat, const u32* col_cat, const long long* vtx_off,
                       const long long* edge_off, u32 G, u32 n, u64 S, u32* rowptr, u32* col,

@@ -175,7 +175,8 @@ __constant__ short kNzVal[kMaxNz];
 __constant__ unsigned short kRowStart[74];
 
 __global__ void __launch_bounds__(kFinalThreads)
-finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ out) {
+finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ out,
+                const u32* __restrict__ old_of) {
   __shared__ long long s_out[kFinalThreads * 73];
   const u32 n = g.n;
   const u32 u0 = blockIdx.x * kFinalThreads;
@@ -274,8 +275,15 @@ finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ ou
   }
   __syncthreads();
   const u32 cnt = min((u32)kFinalThreads, n - u0);
-  long long* dst = out + (u64)u0 * 73;
-  for (u32 i = threadIdx.x; i < cnt * 73; i += kFinalThreads) dst[i] = s_out[i];
+  if (!old_of) {
+    long long* dst = out + (u64)u0 * 73;
+    for (u32 i = threadIdx.x; i < cnt * 73; i += kFinalThreads) dst[i] = s_out[i];
+  } else {  // relabelled graph: row of vertex u0 + r goes to its caller id
+    for (u32 i = threadIdx.x; i < cnt * 73; i += kFinalThreads) {
+      const u32 r = i / 73, k = i % 73;
+      out[(u64)old_of[u0 + r] * 73 + k] = s_out[i];
+    }
+  }
 }
 
 inline unsigned warp_blocks(u32 n) { return (unsigned)(((u64)n * 32 + 255) / 256); }
@@ -318,7 +326,9 @@ int upload_transform(const long long* A) {
   return nz;
 }
 
-void launch_finalize(const Graph& g, const u64* acc, long long* out, cudaStream_t st) {
+void launch_finalize(const Graph& g, const u64* acc, long long* out, const u32* old_of,
+                     cudaStream_t st) {
   if (!g.n) return;
-  finalize_kernel<<<(g.n + kFinalThreads - 1) / kFinalThreads, kFinalThreads, 0, st>>>(g, acc, out);
+  finalize_kernel<<<(g.n + kFinalThreads - 1) / kFinalThreads, kFinalThreads, 0, st>>>(g, acc, out,
+                                                                                     old_of);
 }
