@@ -179,7 +179,6 @@ void launch_tri_fill(const Graph& g, const u32* T, cudaStream_t st);
 void launch_tri_edge(const Graph& g, const SlotArrays& sa, cudaStream_t st);
 void launch_vsum1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_tri_opp1(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
-void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 // A CTA's dense 2-hop map, one entry per vertex id (within a component for
 // batches), split by access frequency: every wedge touches the 16-byte hot
 // record; only vertices on the root's directed 3-paths touch the cold one.

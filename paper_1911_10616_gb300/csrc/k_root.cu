@@ -533,12 +533,7 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
   __syncwarp();
   for (u64 s = gw; s < g.S; s += nwarps) {
     if (sa.T[s] < 2) continue;
-    u32 lo = 0, hi = g.n;
-    while (hi - lo > 1) {
-      u32 mid = lo + ((hi - lo) >> 1);
-      if (g.rowptr[mid] <= (u32)s) lo = mid;
-      else hi = mid;
-    }
+    const u32 lo = g.col[g.rev[s]];  // the row owning slot s
     const u32 ub = g.rowptr[lo], du = g.rowptr[lo + 1] - ub;
     const bool small = du <= kLinkSmem;
     u32* list = small ? s_list[wid] : glist;
@@ -674,14 +669,7 @@ k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
   const u32 gw = blockIdx.x * kK5Warps + wid;
   const u32 nw = gridDim.x * kK5Warps;
   for (u32 e = gw; e < m; e += nw) {
-    // source of DAG edge e
-    u32 lo = 0, hi = g.n;
-    while (hi - lo > 1) {
-      u32 mid = lo + ((hi - lo) >> 1);
-      if (g.dag_ptr[mid] <= e) lo = mid;
-      else hi = mid;
-    }
-    const u32 a = lo, b = g.dag_col[e];
+    const u32 a = g.col[g.rev[g.dag_slot[e]]], b = g.dag_col[e];  // source, target of DAG edge e
     u32 xb = g.dag_ptr[a], xe = g.dag_ptr[a + 1];
     u32 yb = g.dag_ptr[b], ye = g.dag_ptr[b + 1];
     if (xe - xb < 3 || ye - yb < 3) continue;

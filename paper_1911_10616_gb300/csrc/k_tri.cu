@@ -31,7 +31,7 @@ __global__ void tri_kernel(Graph g, u32* __restrict__ T, u32 m) {
   const u32 e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= m) return;
   const u32 s = g.dag_slot[e];
-  const u32 u = row_of(g.rowptr, g.n, s);
+  const u32 u = g.col[g.rev[s]];  // the row owning slot s
   const u32 v = g.col[s];
   const u32 ub = g.rowptr[u], ue = g.rowptr[u + 1];
   const u32 vb = g.rowptr[v], ve = g.rowptr[v + 1];
@@ -69,7 +69,7 @@ __global__ void tri_kernel(Graph g, u32* __restrict__ T, u32 m) {
 __global__ void tri_edge_kernel(Graph g, SlotArrays sa) {
   const u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.S) return;
-  const u32 u = row_of(g.rowptr, g.n, (u32)s);
+  const u32 u = g.col[g.rev[s]];  // the row owning slot s
   const u32 v = g.col[s];
   u64 e7 = 0, e9 = 0;
   u32 mid = 0, top = 0;
@@ -134,66 +134,104 @@ __global__ void tri_opp_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   }
 }
 
-// one thread per triangle-list entry; the entry (slot (a,b), x = c) is the
-// triangle's single representative when a precedes b precedes c.  Then
-// K4(t) = |N(a)^N(b)^N(c)| = |tl(a,b) ^ tl(a,c)| (both ascending slot lists).
-__global__ void k4_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, u64 total) {
-  const u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= total) return;
-  // slot owning entry q
-  u64 lo = 0, hi = g.S;
-  while (hi - lo > 1) {
-    u64 mid = lo + ((hi - lo) >> 1);
-    if (g.tl_ptr[mid] <= q) lo = mid;
-    else hi = mid;
-  }
-  const u32 s = (u32)lo;
-  const u32 a = row_of(g.rowptr, g.n, s);
-  const u32 b = g.col[s];
-  if (!prec(g.deg, a, b)) return;
-  const u32 sac = g.tl[q];
-  const u32 c = g.col[sac];
-  if (!prec(g.deg, b, c)) return;
-  const u32 r = g.rev[s];
-  const u32 sbc = g.tl[g.tl_ptr[r] + (q - g.tl_ptr[s])];
-  // merge-intersect tl(a,b) and tl(a,c)
+// One warp per DAG edge a -> b (slot s of b in row a); lanes take the
+// triangle-list entries c of (a,b) with b preceding c, so every triangle
+// a < b < c (degree order) is seen once.  K4(t) = |N(a)^N(b)^N(c)| =
+// |tl(a,b) ^ tl(a,c)| (both ascending slot lists of row a).  Every apex of
+// these triangles lies in tl(a,b): the warp sums the apex credits per list
+// position in shared memory and adds them once per apex; the credits of a,
+// b and of the edge (a,b) are summed over the warp.
+constexpr int kK4Warps = 8;
+constexpr u32 kK4Pos = 1024;
+
+__global__ void __launch_bounds__(kK4Warps * 32)
+k4_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, u32 m) {
+  __shared__ u32 s70[kK4Warps][kK4Pos];
+  __shared__ u32 s66[kK4Warps][kK4Pos];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 e = blockIdx.x * kK4Warps + wid;
+  if (e >= m) return;
+  const u32 s = g.dag_slot[e];
   const u64 p0 = g.tl_ptr[s], p1 = g.tl_ptr[s + 1];
-  const u64 q0 = g.tl_ptr[sac], q1 = g.tl_ptr[sac + 1];
-  u64 i = p0, j = q0;
-  u32 k4 = 0;
-  while (i < p1 && j < q1) {
-    const u32 x = g.tl[i], y = g.tl[j];
-    if (x < y) ++i;
-    else if (y < x) ++j;
-    else { ++k4; ++i; ++j; }
-  }
-  if (!k4) return;
+  if (p1 - p0 < 1) return;
+  const u32 b = g.col[s];
+  const u32 r = g.rev[s];
+  const u32 a = g.col[r];
   const u32 n = g.n;
-  atomicAdd(&sa.K4[s], (u64)k4);
-  atomicAdd(&sa.K4[r], (u64)k4);
-  atomicAdd(&sa.K4[sac], (u64)k4);
-  atomicAdd(&sa.K4[g.rev[sac]], (u64)k4);
-  atomicAdd(&sa.K4[sbc], (u64)k4);
-  atomicAdd(&sa.K4[g.rev[sbc]], (u64)k4);
-  const u64 k2 = c2(k4);
-  if (k2) {
-    atomicAdd(&acc[(u64)A_S71 * n + a], k2);
-    atomicAdd(&acc[(u64)A_S71 * n + b], k2);
-    atomicAdd(&acc[(u64)A_S71 * n + c], k2);
+  const u64 r0 = g.tl_ptr[r];
+  const bool local = p1 - p0 <= kK4Pos;
+  if (local) {
+    for (u32 i = lane; i < p1 - p0; i += 32) s70[wid][i] = s66[wid][i] = 0;
+    __syncwarp();
   }
-  const u64 tsum = (u64)sa.T[s] + sa.T[sac] + sa.T[sbc];
-  i = p0;
-  j = q0;
-  while (i < p1 && j < q1) {
-    const u32 x = g.tl[i], y = g.tl[j];
-    if (x < y) ++i;
-    else if (y < x) ++j;
-    else {
-      const u32 apex = g.tlv[i];  // vertex id of entry i of tl(a,b)
-      if (k4 > 1) atomicAdd(&acc[(u64)A_S70 * n + apex], (u64)(k4 - 1));
-      atomicAdd(&acc[(u64)A_S66 * n + apex], tsum);
-      ++i;
-      ++j;
+  u64 k4ab = 0, k2ab = 0;
+  for (u64 q = p0 + lane; q < p1; q += 32) {
+    const u32 c = g.tlv[q];
+    if (!prec(g.deg, b, c)) continue;
+    const u32 sac = g.tl[q];
+    const u32 sbc = g.tl[r0 + (q - p0)];
+    const u64 q0 = g.tl_ptr[sac], q1 = g.tl_ptr[sac + 1];
+    u64 i = p0, j = q0;
+    u32 k4 = 0;
+    while (i < p1 && j < q1) {
+      const u32 x = g.tl[i], y = g.tl[j];
+      if (x < y) ++i;
+      else if (y < x) ++j;
+      else { ++k4; ++i; ++j; }
+    }
+    if (!k4) continue;
+    k4ab += k4;
+    atomicAdd(&sa.K4[sac], (u64)k4);
+    atomicAdd(&sa.K4[g.rev[sac]], (u64)k4);
+    atomicAdd(&sa.K4[sbc], (u64)k4);
+    atomicAdd(&sa.K4[g.rev[sbc]], (u64)k4);
+    const u64 k2 = c2(k4);
+    if (k2) {
+      k2ab += k2;
+      atomicAdd(&acc[(u64)A_S71 * n + c], k2);
+    }
+    const u32 tsum = sa.T[s] + sa.T[sac] + sa.T[sbc];
+    i = p0;
+    j = q0;
+    while (i < p1 && j < q1) {
+      const u32 x = g.tl[i], y = g.tl[j];
+      if (x < y) ++i;
+      else if (y < x) ++j;
+      else {
+        if (local) {
+          if (k4 > 1) atomicAdd(&s70[wid][i - p0], k4 - 1);
+          atomicAdd(&s66[wid][i - p0], tsum);
+        } else {
+          const u32 apex = g.tlv[i];
+          if (k4 > 1) atomicAdd(&acc[(u64)A_S70 * n + apex], (u64)(k4 - 1));
+          atomicAdd(&acc[(u64)A_S66 * n + apex], (u64)tsum);
+        }
+        ++i;
+        ++j;
+      }
+    }
+  }
+  k4ab = warp_sum(k4ab);
+  k2ab = warp_sum(k2ab);
+  if (lane == 0) {
+    if (k4ab) {
+      atomicAdd(&sa.K4[s], k4ab);
+      atomicAdd(&sa.K4[r], k4ab);
+    }
+    if (k2ab) {
+      atomicAdd(&acc[(u64)A_S71 * n + a], k2ab);
+      atomicAdd(&acc[(u64)A_S71 * n + b], k2ab);
+    }
+  }
+  if (local) {
+    __syncwarp();
+    for (u32 i = lane; i < p1 - p0; i += 32) {
+      const u32 v70 = s70[wid][i], v66 = s66[wid][i];
+      if (v70 | v66) {
+        const u32 apex = g.tlv[p0 + i];
+        if (v70) atomicAdd(&acc[(u64)A_S70 * n + apex], (u64)v70);
+        if (v66) atomicAdd(&acc[(u64)A_S66 * n + apex], (u64)v66);
+      }
     }
   }
 }
@@ -237,15 +275,9 @@ void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_
 
 void launch_k4_known(const Graph& g, const SlotArrays& sa, u64* acc, u64 total, cudaStream_t st) {
   if (!g.S) return;
-  if (total) k4_kernel<<<blocks_for(total, 256), 256, 0, st>>>(g, sa, acc, total);
+  const u32 m = (u32)(g.S / 2);
+  if (total) k4_kernel<<<(m + kK4Warps - 1) / kK4Warps, kK4Warps * 32, 0, st>>>(g, sa, acc, m);
   halve_kernel<<<blocks_for(g.S, 256), 256, 0, st>>>(sa.K4, g.S);
 }
 
-void launch_k4(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {
-  if (!g.S) return;
-  u64 total = 0;
-  cudaMemcpyAsync(&total, g.tl_ptr + g.S, sizeof(u64), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  if (total) k4_kernel<<<blocks_for(total, 256), 256, 0, st>>>(g, sa, acc, total);
-  halve_kernel<<<blocks_for(g.S, 256), 256, 0, st>>>(sa.K4, g.S);
-}
+
