@@ -57,7 +57,16 @@ WORKLOADS = {
                         "R-MAT scale 16 (small learned-schedule check)"),
     "batch_20k": (dict(kind="batch", graphs=20_000, nmin=10, nmax=500),
                   "20,000 graphs, n ~ U[10,500], 1/3 each ER / BA / RGG"),
+    "chung_lu_1m_four": (dict(kind="chung_lu", n=1_000_000, m=10_000_000, exponent=2.1,
+                              cap=5000, orbits=15),
+                         "Chung-Lu n=1,000,000 m~10,000,000 exponent 2.1 degree cap 5,000; "
+                         "4-vertex orbits 0-14 only"),
 }
+METRIC_FOUR = "edges/s to the 15 vertex orbits of 2- to 4-vertex graphlets"
+
+
+def metric_of(spec):
+    return METRIC_FOUR if spec.get("orbits", 73) == 15 else METRIC
 
 
 def make_graph(spec, seed):
@@ -162,10 +171,11 @@ def cpu_oracle_baseline(spec_name, seed, budget_s=20.0):
     import oracle
     spec = dict(WORKLOADS[spec_name][0])
     threads = oracle.max_threads()
+    method = oracle.formulas4 if spec.get("orbits", 73) == 15 else oracle.formulas
     if spec["kind"] == "er":
         g = make_graph(spec, seed)
         t0 = time.perf_counter()
-        oracle.formulas(g, threads)
+        method(g, threads)
         dt = time.perf_counter() - t0
         return {"value": g.m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                 "sample": f"the full workload ({g})", "seconds": dt}
@@ -177,7 +187,7 @@ def cpu_oracle_baseline(spec_name, seed, budget_s=20.0):
         sub["m"] = max(5000, int(spec["m"] * frac))
         g = make_graph(sub, seed)
         t0 = time.perf_counter()
-        oracle.formulas(g, threads)
+        method(g, threads)
         dt = time.perf_counter() - t0
         best = {"value": g.m / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                 "sample": (f"same generator at {frac:.3g} of the vertices and edges "
@@ -201,7 +211,8 @@ def run_reference(args, rank, world):
     secs = [r["seconds"] for r in res]
     value = statistics.median([r["value"] for r in res])
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "impl": "reference", "metric": metric_of(WORKLOADS[spec_name][0]), "value": value,
+        "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * statistics.median(secs), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -241,7 +252,7 @@ def max_over_ranks(x, dist):
     return float(t.item())
 
 
-def roofline_of(phases, g, ev, rp, col, n, m, args):
+def roofline_of(phases, g, ev, rp, col, n, m, args, four=False):
     peak, peak_kind = read_peaks()
     if not phases:
         return None
@@ -249,8 +260,13 @@ def roofline_of(phases, g, ev, rp, col, n, m, args):
     per_launch_s = ms / 1000.0 / max(nl, 1)
     ent = None
     if name == "root" and g is not None and not args.no_roofline:
-        T_slot = ev.edge_orbits(rp, col, n, m)["T"].cpu().numpy()
-        ent = root_pass_entries(g, T_slot)
+        if four:  # one wedge sweep (W and C4(u)) and nothing else
+            d = g.degrees().astype(np.int64)
+            ent = {"sum_d2": int((d * d).sum())}
+            ent["entries"] = ent["sum_d2"]
+        else:
+            T_slot = ev.edge_orbits(rp, col, n, m)["T"].cpu().numpy()
+            ent = root_pass_entries(g, T_slot)
         alg_bytes = 4 * ent["entries"]
     else:
         alg_bytes = 4 * (2 * m) + 8 * n  # lower bound: one read of the CSR
@@ -266,6 +282,7 @@ def run_single(args, rank, world, dist, barrier):
     from paper_1911_10616_gb300 import _lib
 
     spec, desc = WORKLOADS[args.workload]
+    orbits = spec.get("orbits", 73)
     seed = 1 + rank
     t0 = time.perf_counter()
     g = make_graph(spec, seed)
@@ -274,7 +291,7 @@ def run_single(args, rank, world, dist, barrier):
     rp, col = ev.to_device(g)
     n, m = g.n, g.m
     stream = torch.cuda.current_stream()
-    plan = ev.Plan.single(rp, col, n, m, validate=True)
+    plan = ev.Plan.single(rp, col, n, m, validate=True, orbits=orbits)
     out = plan.new_output()
     plan.execute(out)
     # autotune the per-root pass shape (threads per CTA x persistent CTAs)
@@ -314,14 +331,14 @@ def run_single(args, rank, world, dist, barrier):
     if args.e2e_steps > 0:
         h_rp = torch.from_numpy(g.rowptr.astype(np.uint32).view(np.int32)).pin_memory()
         h_col = torch.from_numpy(g.col.astype(np.uint32).view(np.int32)).pin_memory()
-        h_out = torch.empty((n, 73), dtype=torch.int64).pin_memory()
+        h_out = torch.empty((n, orbits), dtype=torch.int64).pin_memory()
         d_rp = torch.empty_like(rp)
         d_col = torch.empty_like(col)
 
         def e2e_step():
             d_rp.copy_(h_rp, non_blocking=True)
             d_col.copy_(h_col, non_blocking=True)
-            ev.count_orbits(d_rp, d_col, n, m, out=out)
+            ev.count_orbits(d_rp, d_col, n, m, out=out, orbits=orbits)
             h_out.copy_(out, non_blocking=True)
 
         e2e_t = max(max_over_ranks(timed(e2e_step, args.e2e_steps, stream, barrier), dist), 1e-12)
@@ -331,7 +348,7 @@ def run_single(args, rank, world, dist, barrier):
     if rank != 0:
         return None
     info = plan.info()
-    roof = roofline_of(phases, g, ev, rp, col, n, m, args)
+    roof = roofline_of(phases, g, ev, rp, col, n, m, args, four=orbits == 15)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -340,7 +357,8 @@ def run_single(args, rank, world, dist, barrier):
         except Exception as exc:  # report, never fake
             cpu = {"error": repr(exc)}
     return {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric_of(spec), "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",

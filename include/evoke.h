@@ -54,15 +54,19 @@ typedef struct evoke_opts {
   int32_t validate;   /* nonzero: check the CSR invariants first (syncs the stream) */
   int32_t root_ctas;  /* persistent CTAs of the per-root pass; 0 = 2 per SM */
   int32_t schedule;   /* 0 = degree-bucket schedule (decreasing wedge work) */
-  int32_t reserved;
+  int32_t orbits;     /* 0 or 73: all 73 orbits, out is int64[n*73];
+                         15: the 4-vertex orbits 0..14 only (Thm. 4orbit,
+                         Lem. 4vertexorbit), out is int64[n*15] and the
+                         5-vertex passes are skipped; other values: EVOKE_EINVAL */
 } evoke_opts;
 
 /*
  * evoke_count_orbits -- induced orbit counts of all vertices.
  *   rowptr, colidx : device CSR as described above (read only).
  *   n, m           : vertices and undirected edges (colidx has 2m entries).
- *   out            : device int64[n*73], row-major, orbit index = the
- *                    paper's orbit number (Fig. node_orbits); fully written.
+ *   out            : device int64[n*73] (n*15 with opts->orbits = 15),
+ *                    row-major, orbit index = the paper's orbit number
+ *                    (Fig. node_orbits); fully written.
  *   opts           : may be NULL (defaults: no validation, 2 CTAs per SM).
  * Synchronises `stream` (buffer sizing).  Errors: EVOKE_EINVAL (null
  * pointers with n > 0, rowptr[n] != 2m), EVOKE_ENOTSIMPLE / EVOKE_ERANGE
@@ -120,6 +124,7 @@ typedef struct evoke_plan_stats {
   int32_t root_ctas;          /* persistent CTAs of the per-root pass */
   int32_t root_ctas_max;      /* most CTAs evoke_plan_set_tuning accepts */
   int32_t link_warps;
+  int32_t orbits;             /* orbits per output row: 73, or 15 */
 } evoke_plan_stats;
 
 int evoke_plan_create(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
@@ -226,6 +231,21 @@ int evoke_build_dag_noalloc(const uint32_t* rowptr, const uint32_t* colidx, uint
 int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
                       int64_t* tri, int64_t* c4, int64_t* k4, int64_t* e7, int64_t* e9,
                       void* stream);
+
+/*
+ * evoke_edge_orbit_counts -- the twelve edge orbits E0..E11 of the 3- and
+ * 4-vertex patterns (Fig. edge_orbits), non-induced, per Lem. 4edgeorbit.
+ * out: device int64[2m * 12], row s = CSR slot s = (u,v) (the slot of v in
+ * row u), column i = E_i<u,v>: the number of distinct non-induced copies of
+ * the orbit's pattern in which (u,v) lies in edge orbit i and, where the two
+ * ends of the edge orbit lie in different vertex orbits, u lies in the one
+ * with the larger orbit number (e.g. E0<u,v> = d(u) - 1, u the centre of the
+ * 2-path).  Symmetric orbits (E1, E3, E5, E7, E10, E11) give the same value
+ * in slots (u,v) and (v,u).  The caller owns `out`.  Synchronises `stream`.
+ * Errors as evoke_count_orbits; EVOKE_EINVAL if out is NULL and m > 0.
+ */
+int evoke_edge_orbit_counts(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n,
+                            uint64_t m, int64_t* out, void* stream);
 
 /*
  * evoke_orbit_matrix -- the library's matrix A of App. A (DM = A * DIM),

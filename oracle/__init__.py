@@ -50,6 +50,9 @@ def _load():
             lib.oracle_brute_force.argtypes = [i64p, u32p, ctypes.c_uint32, i64p, i64p, ctypes.c_int]
             lib.oracle_formulas.argtypes = [i64p, u32p, ctypes.c_uint32, i64p, i64p, ctypes.c_int]
             lib.oracle_edge_counts.argtypes = [i64p, u32p, ctypes.c_uint32] + [i64p] * 5 + [ctypes.c_int]
+            lib.oracle_edge_orbits_brute.argtypes = [i64p, u32p, ctypes.c_uint32, i64p, ctypes.c_int]
+            lib.oracle_edge_orbits_formula.argtypes = [i64p, u32p, ctypes.c_uint32, i64p, ctypes.c_int]
+            lib.oracle_formulas4.argtypes = [i64p, u32p, ctypes.c_uint32, i64p, ctypes.c_int]
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -127,6 +130,17 @@ def induced(g, threads: int = 0) -> np.ndarray:
     return formulas(g, threads)[1]
 
 
+def formulas4(g, threads: int = 0):
+    """Induced counts of the 4-vertex orbits 0..14 only (Thm. 4orbit), int64[n,15]."""
+    rp, col = _csr(g)
+    dim = np.zeros(g.n * 15, np.int64)
+    rc = _load().oracle_formulas4(_p(rp, ctypes.c_int64), _p(col, ctypes.c_uint32), g.n,
+                                  _p(dim, ctypes.c_int64), threads)
+    if rc:
+        raise RuntimeError(f"oracle 4-vertex formulas failed ({rc})")
+    return dim.reshape(g.n, 15)
+
+
 def edge_counts(g, threads: int = 0):
     """Per-slot T, C4, K4, E7, E9<u,v> (slot = position of v in row u)."""
     rp, col = _csr(g)
@@ -137,6 +151,26 @@ def edge_counts(g, threads: int = 0):
     if rc:
         raise RuntimeError(f"oracle edge counts failed ({rc})")
     return dict(zip(["T", "C4", "K4", "E7", "E9"], outs))
+
+
+def _edge_orbits(fn, what, g, threads):
+    rp, col = _csr(g)
+    S = int(rp[-1])
+    out = np.zeros((S, 12), np.int64)
+    rc = fn(_p(rp, ctypes.c_int64), _p(col, ctypes.c_uint32), g.n, _p(out, ctypes.c_int64), threads)
+    if rc:
+        raise RuntimeError(f"oracle {what} failed ({rc})")
+    return out
+
+
+def edge_orbits_brute(g, threads: int = 0):
+    """E0..E11<u,v> per slot by the definition (tiny graphs): int64 [2m, 12]."""
+    return _edge_orbits(_load().oracle_edge_orbits_brute, "edge-orbit brute force", g, threads)
+
+
+def edge_orbits_formula(g, threads: int = 0):
+    """E0..E11<u,v> per slot by Lem. 4edgeorbit: int64 [2m, 12]."""
+    return _edge_orbits(_load().oracle_edge_orbits_formula, "edge-orbit formulas", g, threads)
 
 
 def max_threads() -> int:

@@ -87,6 +87,20 @@ const PatternDef kPatterns[30] = {
     {5, "12 13 14 15 23 24 25 34 35 45", "5:72"},                // H29
 };
 
+// Edge orbits of the 3- and 4-vertex patterns (Fig. edge_orbits), numbered as
+// in Lem. 4edgeorbit: the pattern and the vertex orbits of the edge's two
+// ends, larger first.  READING: the figure's labels sit between edges in the
+// extracted text; the numbering is fixed by the lemma's equations instead
+// (E0 = d(u)-1 is the 2-path, E2 / E3 the end / middle edges of the 3-path,
+// E6 / E7 / E8 the paw's pendant edge / edge opposite the centre / edges at
+// the centre on the triangle, E9 / E10 the diamond's outer edges / chord).
+struct EdgeOrbitDef {
+  int pattern, hi, lo;
+};
+const EdgeOrbitDef kEdgeOrbits[12] = {
+    {1, 2, 1},   {2, 3, 3},   {3, 5, 4},    {3, 5, 5},   {4, 7, 6},    {5, 8, 8},
+    {6, 11, 9},  {6, 10, 10}, {6, 11, 10},  {7, 13, 12}, {7, 13, 13},  {8, 14, 14}};
+
 struct Pattern {
   int k = 0;
   int adj[5][5] = {};
@@ -102,6 +116,9 @@ struct Tables {
   // classification of a k-vertex adjacency mask: per position, the orbit, or -1
   std::vector<std::vector<std::array<int, 5>>> cls;  // cls[k][mask]
   ll A[73][73] = {};      // DM = A * DIM (App. A)
+  // edge orbit of an edge whose ends have vertex orbits (hi, lo), hi >= lo,
+  // in a 3- or 4-vertex pattern; -1 if none
+  int edge_orbit[15][15];
 };
 
 inline int pair_bit(int i, int j) {  // i < j < 5, bit index among C(5,2) pairs
@@ -235,6 +252,53 @@ Tables build_tables() {
           for (int i = 0; i < 73; ++i)
             if (cnt[a][i] != cnt[b][i]) return t;
   }
+  // edge orbits: every edge of H1..H8 falls in exactly one row of the table,
+  // and the rows are the automorphism classes of the edges (Def. auto)
+  for (int a = 0; a < 15; ++a)
+    for (int b = 0; b < 15; ++b) t.edge_orbit[a][b] = -1;
+  for (int r = 0; r < 12; ++r) {
+    const EdgeOrbitDef& e = kEdgeOrbits[r];
+    if (e.hi < e.lo || e.hi > 14 || t.edge_orbit[e.hi][e.lo] != -1) return t;
+    if (t.orbit_pattern[e.hi] != e.pattern || t.orbit_pattern[e.lo] != e.pattern) return t;
+    t.edge_orbit[e.hi][e.lo] = r;
+  }
+  for (int j = 1; j <= 8; ++j) {
+    const Pattern& p = t.pat[j];
+    int ecls[5][5];
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) ecls[a][b] = -1;
+    for (int a = 0; a < p.k; ++a)
+      for (int b = a + 1; b < p.k; ++b)
+        if (p.adj[a][b]) {
+          const int r = t.edge_orbit[std::max(p.orbit[a], p.orbit[b])][std::min(p.orbit[a], p.orbit[b])];
+          if (r < 0) return t;
+          ecls[a][b] = r;
+        }
+    // edges related by an automorphism share a row; edges sharing a row are
+    // related by one
+    int perm[5] = {0, 1, 2, 3, 4};
+    bool linked[5][5][5][5] = {};
+    do {
+      bool aut = true;
+      for (int a = 0; a < p.k && aut; ++a)
+        for (int b = 0; b < p.k; ++b)
+          if (p.adj[a][b] != p.adj[perm[a]][perm[b]]) { aut = false; break; }
+      if (!aut) continue;
+      for (int a = 0; a < p.k; ++a)
+        for (int b = a + 1; b < p.k; ++b)
+          if (p.adj[a][b]) {
+            int c = std::min(perm[a], perm[b]), d = std::max(perm[a], perm[b]);
+            if (ecls[a][b] != ecls[c][d]) return t;
+            linked[a][b][c][d] = true;
+          }
+    } while (std::next_permutation(perm, perm + p.k));
+    for (int a = 0; a < p.k; ++a)
+      for (int b = a + 1; b < p.k; ++b)
+        for (int c = 0; c < p.k; ++c)
+          for (int d = c + 1; d < p.k; ++d)
+            if (p.adj[a][b] && p.adj[c][d] && ecls[a][b] == ecls[c][d] && !linked[a][b][c][d])
+              return t;
+  }
   t.ok = true;
   return t;
 }
@@ -323,6 +387,8 @@ struct Esu {
   uint32_t root;
   uint32_t sub[5] = {0, 0, 0, 0, 0};
   int ns = 0;
+  ll* eo = nullptr;  // optional [2m*12]: edge-orbit matches per slot (Lem. 4edgeorbit)
+  int kmax = 5;      // largest subset enumerated
 
   bool in_sub(uint32_t x) const {
     for (int i = 0; i < ns; ++i)
@@ -355,10 +421,30 @@ struct Esu {
         for (int a = 0; a < ns; ++a) dm[(size_t)sub[a] * 73 + cc[a]]++;
       }
     }
+    if (eo && (ns == 3 || ns == 4)) {
+      // every non-induced copy (connected spanning edge subset) and each of
+      // its edges: +1 on the edge orbit, in the slot leaving the end with the
+      // larger vertex orbit (both slots when the ends share an orbit)
+      for (int s = 1; s < (1 << ne); ++s) {
+        int sm = 0;
+        for (int e = 0; e < ne; ++e)
+          if (s >> e & 1) sm |= 1 << pair_bit(pe[e][0], pe[e][1]);
+        if (!connected_mask(ns, sm)) continue;
+        const auto& cc = t.cls[ns][sm];
+        for (int e = 0; e < ne; ++e) {
+          if (!(s >> e & 1)) continue;
+          const int a = pe[e][0], b = pe[e][1];
+          const int oa = cc[a], ob = cc[b];
+          const int r = t.edge_orbit[std::max(oa, ob)][std::min(oa, ob)];
+          if (oa >= ob) eo[(size_t)g.slot(sub[a], sub[b]) * 12 + r]++;
+          if (ob >= oa) eo[(size_t)g.slot(sub[b], sub[a]) * 12 + r]++;
+        }
+      }
+    }
   }
   void extend(std::vector<uint32_t> ext) {
     if (ns >= 2) report();
-    if (ns == 5) return;
+    if (ns == kmax) return;
     while (!ext.empty()) {
       uint32_t w = ext.back();
       ext.pop_back();
@@ -387,6 +473,7 @@ struct Formula {
   // per slot (u,v): T(u,v), C4(u,v), K4(u,v), E7, E9<u,v>
   std::vector<ll> Te, C4e, K4e, E7e, E9e;
   bool overflow = false;
+  bool four_only = false;      // stop after Lem. 4vertexorbit (orbits 0..14)
 
   explicit Formula(const G& gg, int th) : g(gg), threads(th) {}
 
@@ -410,7 +497,7 @@ void Formula::run() {
 
   // C4(u,v): 4-cycles u-v-b-a-u through the edge, by direct enumeration
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
-  for (int64_t u = 0; u < (int64_t)n; ++u)
+  for (int64_t u = 0; u < (int64_t)(four_only ? 0 : n); ++u)
     for (int64_t s = g.rp[u]; s < g.rp[u + 1]; ++s) {
       uint32_t v = g.col[s];
       ll c = 0;
@@ -453,7 +540,7 @@ void Formula::run() {
   }
   // triangle-based edge counts E7, E9 (Lem. 4edgeorbit)
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
-  for (int64_t u = 0; u < (int64_t)n; ++u)
+  for (int64_t u = 0; u < (int64_t)(four_only ? 0 : n); ++u)
     for (int64_t s = g.rp[u]; s < g.rp[u + 1]; ++s) {
       uint32_t v = g.col[s];
       ll e7 = 0, e9 = 0;
@@ -508,6 +595,8 @@ void Formula::run() {
     }
     dm(u, 12) = s12;
   }
+
+  if (four_only) return;
 
   // --- Thm. 5vertexorbit ------------------------------------------------------
   // pair quantities, from plain definitions
@@ -926,6 +1015,26 @@ int oracle_formulas(const int64_t* rowptr, const uint32_t* col, uint32_t n, int6
   return rc;
 }
 
+// The 4-vertex orbits only (Thm. 4orbit: Lem. 4vertexorbit, then the 4-vertex
+// block of A^-1).  dim: n*15 induced counts of orbits 0..14.
+int oracle_formulas4(const int64_t* rowptr, const uint32_t* col, uint32_t n, int64_t* dim,
+                     int threads) {
+  const Tables& t = tables();
+  if (!t.ok) return 1;
+  G g{n, rowptr, col};
+  Formula f(g, threads);
+  f.four_only = true;
+  f.run();
+  int rc = f.overflow ? 7 : 0;
+  std::vector<i128> out(73);
+  for (uint32_t u = 0; u < n; ++u) {
+    // orbits 15..72 of f.DM are zero; A is block diagonal by pattern size
+    if (!invert_apply(t, &f.DM[(size_t)u * 73], out.data())) rc = 7;
+    rc |= store(out.data(), dim + (size_t)u * 15, 15);
+  }
+  return rc;
+}
+
 // Per-slot edge quantities of Lem. 4edgeorbit and per-vertex T, C4, K4, for
 // intermediate checks: each output array has rowptr[n] entries (slot (u,v) =
 // position of v in row u); E9 is the ordered count E9<u,v>.
@@ -941,6 +1050,78 @@ int oracle_edge_counts(const int64_t* rowptr, const uint32_t* col, uint32_t n, i
     T[s] = f.Te[s]; C4[s] = f.C4e[s]; K4[s] = f.K4e[s]; E7[s] = f.E7e[s]; E9[s] = f.E9e[s];
   }
   return f.overflow ? 7 : 0;
+}
+
+// Edge orbits by the definition: out [rowptr[n] * 12], row = slot (u,v),
+// column i = E_i<u,v> (Fig. edge_orbits, the Definition after it), by
+// enumerating every connected 3- and 4-vertex subset and its connected
+// spanning edge subsets.  Tiny graphs only.
+int oracle_edge_orbits_brute(const int64_t* rowptr, const uint32_t* col, uint32_t n, int64_t* out,
+                             int threads) {
+  const Tables& t = tables();
+  if (!t.ok) return 1;
+  G g{n, rowptr, col};
+  const int nt = nthreads_of(threads);
+  const size_t S = (size_t)rowptr[n];
+  std::vector<std::vector<ll>> pe(nt, std::vector<ll>(S * 12, 0));
+  std::vector<std::vector<ll>> pd(nt, std::vector<ll>((size_t)n * 73, 0));
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (int64_t r = 0; r < (int64_t)n; ++r) {
+    int th = thread_id();
+    Esu e{g, t, pd[th].data(), nullptr, (uint32_t)r};
+    e.eo = pe[th].data();
+    e.kmax = 4;
+    e.sub[0] = (uint32_t)r;
+    e.ns = 1;
+    std::vector<uint32_t> ext;
+    for (int64_t s = rowptr[r]; s < rowptr[r + 1]; ++s)
+      if (col[s] > (uint32_t)r) ext.push_back(col[s]);
+    e.extend(ext);
+  }
+  for (size_t i = 0; i < S * 12; ++i) {
+    ll a = 0;
+    for (int th = 0; th < nt; ++th) a += pe[th][i];
+    out[i] = a;
+  }
+  return 0;
+}
+
+// Edge orbits by Lem. 4edgeorbit, from the base counts of the paper's method.
+int oracle_edge_orbits_formula(const int64_t* rowptr, const uint32_t* col, uint32_t n,
+                               int64_t* out, int threads) {
+  const Tables& t = tables();
+  if (!t.ok) return 1;
+  G g{n, rowptr, col};
+  Formula f(g, threads);
+  f.run();
+  std::vector<i128> Tu(n, 0), dm1(n, 0);  // T(u) and DM1(u) = sum over N(u) of d(v)-1
+  for (uint32_t u = 0; u < n; ++u)
+    for (int64_t s = rowptr[u]; s < rowptr[u + 1]; ++s) {
+      Tu[u] += f.Te[s];
+      dm1[u] += g.deg(col[s]) - 1;
+    }
+  for (uint32_t u = 0; u < n; ++u) Tu[u] /= 2;
+  int rc = f.overflow ? 7 : 0;
+  for (uint32_t u = 0; u < n; ++u)
+    for (int64_t s = rowptr[u]; s < rowptr[u + 1]; ++s) {
+      const uint32_t v = col[s];
+      const i128 du = g.deg(u), dv = g.deg(v), T = f.Te[s];
+      i128 e[12];
+      e[0] = du - 1;
+      e[1] = T;
+      e[2] = (dm1[u] - (dv - 1)) - T;  // sum over x in N(u)\v of (d(x)-1), minus E1
+      e[3] = (du - 1) * (dv - 1) - T;
+      e[4] = C2(du - 1);
+      e[5] = f.C4e[s];
+      e[6] = Tu[u] - T;                 // r(theta_3) matches at u, minus E1
+      e[7] = f.E7e[s];
+      e[8] = T * (du - 2);
+      e[9] = f.E9e[s];
+      e[10] = C2(T);
+      e[11] = f.K4e[s];
+      rc |= store(e, out + (size_t)s * 12, 12);
+    }
+  return rc;
 }
 
 int oracle_max_threads() { return nthreads_of(0); }

@@ -25,7 +25,8 @@ _ERRORS = {
 
 # exported symbols of include/evoke.h
 SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
-           "evoke_build_dag_noalloc", "evoke_edge_orbits", "evoke_orbit_matrix",
+           "evoke_build_dag_noalloc", "evoke_edge_orbits", "evoke_edge_orbit_counts",
+           "evoke_orbit_matrix",
            "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
            "evoke_plan_launch_graph", "evoke_plan_execute_profiled", "evoke_plan_info", "evoke_plan_set_tuning",
            "evoke_plan_destroy", "evoke_plan_set_model", "evoke_plan_features",
@@ -51,12 +52,12 @@ class PlanStats(ctypes.Structure):
                 ("max_component", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
                 ("kernels_per_execution", ctypes.c_int32), ("root_threads", ctypes.c_int32),
                 ("root_ctas", ctypes.c_int32), ("root_ctas_max", ctypes.c_int32),
-                ("link_warps", ctypes.c_int32)]
+                ("link_warps", ctypes.c_int32), ("orbits", ctypes.c_int32)]
 
 
 class EvokeOpts(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("root_ctas", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("orbits", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = True):
         lib.evoke_build_dag_noalloc.restype = ctypes.c_int
         lib.evoke_edge_orbits.argtypes = [vp, vp, u32, u64, vp, vp, vp, vp, vp, vp]
         lib.evoke_edge_orbits.restype = ctypes.c_int
+        lib.evoke_edge_orbit_counts.argtypes = [vp, vp, u32, u64, vp, vp]
+        lib.evoke_edge_orbit_counts.restype = ctypes.c_int
         lib.evoke_orbit_matrix.argtypes = [ctypes.POINTER(ctypes.c_int64)]
         lib.evoke_orbit_matrix.restype = ctypes.c_int
         lib.evoke_strerror.argtypes = [ctypes.c_int]
@@ -161,16 +164,24 @@ def _check_graph(rowptr, colidx, n):
         raise ValueError("rowptr must be contiguous with n+1 entries")
 
 
+def _orbits(orbits: int) -> int:
+    if orbits not in (15, 73):
+        raise ValueError("orbits must be 73 (all) or 15 (the 4-vertex orbits 0..14)")
+    return orbits
+
+
 def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = False,
-                 root_ctas: int = 0, stream=None):
-    """Induced orbit counts, int64 tensor [n, 73] on the graph's device."""
+                 root_ctas: int = 0, stream=None, orbits: int = 73):
+    """Induced orbit counts, int64 tensor [n, orbits] on the graph's device
+    (orbits = 73: all; 15: the 4-vertex orbits 0..14 only)."""
     import torch
     _check_graph(rowptr, colidx, n)
+    k = _orbits(orbits)
     if out is None:
-        out = torch.empty((n, NORB), dtype=torch.int64, device=rowptr.device)
-    elif out.dtype != torch.int64 or out.numel() != n * NORB or not out.is_contiguous():
-        raise ValueError("out must be a contiguous int64 tensor with n*73 entries")
-    opts = EvokeOpts(1 if validate else 0, int(root_ctas), 0, 0)
+        out = torch.empty((n, k), dtype=torch.int64, device=rowptr.device)
+    elif out.dtype != torch.int64 or out.numel() != n * k or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous int64 tensor with n*{k} entries")
+    opts = EvokeOpts(1 if validate else 0, int(root_ctas), 0, k)
     rc = load().evoke_count_orbits(_ptr(rowptr), _ptr(colidx), n, m, _ptr(out),
                                    ctypes.byref(opts), _stream_handle(stream))
     _check(rc, "evoke_count_orbits")
@@ -189,14 +200,15 @@ def batch_to_device(graphs, device="cuda"):
 
 
 def count_batch(rowptr_cat, colidx_cat, vtx_off, edge_off, out=None, validate: bool = False,
-                stream=None):
-    """Induced orbit counts of a batch of graphs, int64 [sum n_g, 73]."""
+                stream=None, orbits: int = 73):
+    """Induced orbit counts of a batch of graphs, int64 [sum n_g, orbits]."""
     import torch
     G = vtx_off.numel() - 1
     N = int(vtx_off[-1].item())
+    k = _orbits(orbits)
     if out is None:
-        out = torch.empty((N, NORB), dtype=torch.int64, device=vtx_off.device)
-    opts = EvokeOpts(1 if validate else 0, 0, 0, 0)
+        out = torch.empty((N, k), dtype=torch.int64, device=vtx_off.device)
+    opts = EvokeOpts(1 if validate else 0, 0, 0, k)
     rc = load().evoke_count_batch(_ptr(rowptr_cat), _ptr(colidx_cat), _ptr(vtx_off),
                                   _ptr(edge_off), G, _ptr(out), ctypes.byref(opts),
                                   _stream_handle(stream))
@@ -208,37 +220,40 @@ class Plan:
     """A sized, allocated execution plan (evoke_plan_*).  Keep the input
     tensors alive and unchanged while the plan exists."""
 
-    def __init__(self, handle, inputs, n):
+    def __init__(self, handle, inputs, n, orbits=73):
         self._h = handle
         self._inputs = inputs
         self.n = n
+        self.orbits = orbits
 
     @classmethod
-    def single(cls, rowptr, colidx, n: int, m: int, validate: bool = False, stream=None):
+    def single(cls, rowptr, colidx, n: int, m: int, validate: bool = False, stream=None,
+               orbits: int = 73):
         _check_graph(rowptr, colidx, n)
         h = ctypes.c_void_p()
-        opts = EvokeOpts(1 if validate else 0, 0, 0, 0)
+        opts = EvokeOpts(1 if validate else 0, 0, 0, _orbits(orbits))
         _check(load().evoke_plan_create(_ptr(rowptr), _ptr(colidx), n, m, ctypes.byref(opts),
                                         _stream_handle(stream), ctypes.byref(h)),
                "evoke_plan_create")
-        return cls(h, (rowptr, colidx), n)
+        return cls(h, (rowptr, colidx), n, orbits)
 
     @classmethod
     def batch(cls, rowptr_cat, colidx_cat, vtx_off, edge_off, validate: bool = False,
-              stream=None):
+              stream=None, orbits: int = 73):
         h = ctypes.c_void_p()
-        opts = EvokeOpts(1 if validate else 0, 0, 0, 0)
+        opts = EvokeOpts(1 if validate else 0, 0, 0, _orbits(orbits))
         G = vtx_off.numel() - 1
         _check(load().evoke_plan_create_batch(_ptr(rowptr_cat), _ptr(colidx_cat), _ptr(vtx_off),
                                               _ptr(edge_off), G, ctypes.byref(opts),
                                               _stream_handle(stream), ctypes.byref(h)),
                "evoke_plan_create_batch")
-        return cls(h, (rowptr_cat, colidx_cat, vtx_off, edge_off), int(vtx_off[-1].item()))
+        return cls(h, (rowptr_cat, colidx_cat, vtx_off, edge_off), int(vtx_off[-1].item()),
+                   orbits)
 
     def new_output(self):
         import torch
         dev = self._inputs[0].device
-        return torch.empty((self.n, NORB), dtype=torch.int64, device=dev)
+        return torch.empty((self.n, self.orbits), dtype=torch.int64, device=dev)
 
     def execute(self, out, stream=None):
         _check(load().evoke_plan_execute(self._h, _ptr(out), _stream_handle(stream)),
@@ -313,6 +328,19 @@ def edge_orbits(rowptr, colidx, n: int, m: int, stream=None):
                                   _stream_handle(stream))
     _check(rc, "evoke_edge_orbits")
     return dict(zip(["T", "C4", "K4", "E7", "E9"], outs))
+
+
+def edge_orbit_counts(rowptr, colidx, n: int, m: int, stream=None):
+    """E0..E11<u,v> of Lem. 4edgeorbit: int64 tensor [2m, 12], row = CSR slot."""
+    import torch
+    _check_graph(rowptr, colidx, n)
+    out = torch.empty((2 * m, 12), dtype=torch.int64, device=rowptr.device)
+    if m == 0:
+        return out
+    rc = load().evoke_edge_orbit_counts(_ptr(rowptr), _ptr(colidx), n, m, _ptr(out),
+                                        _stream_handle(stream))
+    _check(rc, "evoke_edge_orbit_counts")
+    return out
 
 
 def build_dag(rowptr, colidx, n: int, m: int, stream=None):

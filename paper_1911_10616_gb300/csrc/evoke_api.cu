@@ -350,7 +350,14 @@ struct Config {
   int root_threads = 512;
   int root_ctas = 0;      // 0: 2 per SM (512 threads) / 4 per SM (256)
   u32 link_warps = 0;     // 0: 64 per SM
+  int orbits = 73;        // 73, or 15: the 4-vertex orbits only
 };
+
+// evoke_opts.orbits: 0 or 73 -> all orbits, 15 -> orbits 0..14; else -1
+int opts_orbits(const evoke_opts* o) {
+  if (!o || o->orbits == 0 || o->orbits == 73) return 73;
+  return o->orbits == 15 ? 15 : -1;
+}
 
 }  // namespace
 
@@ -651,6 +658,7 @@ int plan_stage2(evoke_plan* P) {
   cudaMemsetAsync(P->block2, 0, ar.used, st);
   P->k5 = k5_configure(P->max_outdeg);
   link_configure();
+  root_configure();
   return EVOKE_OK;
 }
 
@@ -692,8 +700,9 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
   run("dag", n ? 5 : 0, [&] { launch_dag(g, P->cnt, P->scan_tmp, st); });
   run("tri_count", sl, [&] { launch_tri_count(g, sa.T, st); });
   run("tri_scan", S ? 3 : 0, [&] { launch_scan_u32_to_u64(sa.T, g.tl_ptr, S, P->scan_tmp, st); });
+  const bool four = P->cfg.orbits == 15;
   run("tri_fill", sl, [&] { launch_tri_fill(g, sa.T, st); });
-  run("tri_edge", sl, [&] { launch_tri_edge(g, sa, st); });
+  if (!four) run("tri_edge", sl, [&] { launch_tri_edge(g, sa, st); });
   run("vsum1", nl, [&] { launch_vsum1(g, sa, acc, st); });
   run("tri_opp1", nl, [&] { launch_tri_opp1(g, sa, acc, st); });
   run("k4", (P->ntri_entries ? 1 : 0) + sl, [&] { launch_k4_known(g, sa, acc, P->ntri_entries, st); });
@@ -708,16 +717,24 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
   } else {
     run("schedule", 3 * nl, [&] { launch_schedule(g, acc, P->rs, st); });
   }
-  run("root", nl, [&] { launch_root_with_pref(g, sa, acc, P->rs, P->pref, P->pref_stride, st); });
-  run("link", sl, [&] {
-    launch_link(g, sa, P->link_scratch, P->cfg.link_warps, std::max<u32>(P->dmax, 1), st);
+  run("root", nl, [&] {
+    launch_root_with_pref(g, sa, acc, P->rs, P->pref, P->pref_stride, four, st);
   });
-  run("k5", P->k5.blocks ? 1 : 0, [&] { launch_k5(g, acc, P->k5, st); });
-  run("tri_opp2", nl, [&] { launch_tri_opp2(g, sa, acc, st); });
-  run("vsum2", nl, [&] { launch_vsum2(g, sa, acc, st); });
-  run("vsum3", nl, [&] { launch_vsum3(g, acc, st); });
+  if (four) {
+    run("vsum2", nl, [&] { launch_vsum2_four(g, sa, acc, st); });
+  } else {
+    run("link", sl, [&] {
+      launch_link(g, sa, P->link_scratch, P->cfg.link_warps, std::max<u32>(P->dmax, 1), st);
+    });
+    run("k5", P->k5.blocks ? 1 : 0, [&] { launch_k5(g, acc, P->k5, st); });
+    run("tri_opp2", nl, [&] { launch_tri_opp2(g, sa, acc, st); });
+    run("vsum2", nl, [&] { launch_vsum2(g, sa, acc, st); });
+    run("vsum3", nl, [&] { launch_vsum3(g, acc, st); });
+  }
   if (out)
-    run("finalize", nl, [&] { launch_finalize(g, acc, out, P->relabel ? P->rl_old_of : nullptr, st); });
+    run("finalize", nl, [&] {
+      launch_finalize(g, acc, out, P->relabel ? P->rl_old_of : nullptr, P->cfg.orbits, st);
+    });
 }
 
 int count_launches(const evoke_plan* P, bool with_out) {
@@ -725,8 +742,13 @@ int count_launches(const evoke_plan* P, bool with_out) {
   int k = 0;
   if (P->batch) k += 1 + sl;
   if (P->relabel) k += 6 + (P->rl_long_rows ? 1 : 0) + (P->n > P->rl_long_rows ? 1 : 0);
-  k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + sl + nl + nl;
-  k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl + sl + (P->k5.blocks ? 1 : 0) + nl + nl + nl;
+  const bool four = P->cfg.orbits == 15;
+  // degrees, rev, dag, tri_count, tri_scan, tri_fill, [tri_edge], vsum1, tri_opp1
+  k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + (four ? 0 : sl) + nl + nl;
+  // k4, schedule, root
+  k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl;
+  // [link, k5, tri_opp2], vsum2, [vsum3]
+  k += four ? nl : sl + (P->k5.blocks ? 1 : 0) + nl + nl + nl;
   if (P->model) k += 2 * nl;
   if (with_out) k += nl;
   return k;
@@ -766,6 +788,11 @@ int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, ui
   P->m = m;
   P->st = st;
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
+  P->cfg.orbits = opts_orbits(opts);
+  if (P->cfg.orbits < 0) {
+    plan_free(P);
+    return EVOKE_EINVAL;
+  }
   if (opts && opts->validate) {  // validate the caller's CSR before relabelling it
     rc = validate_csr(rowptr, colidx, n, m, st);
     if (rc) {
@@ -902,6 +929,11 @@ int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_c
   P->m = (u64)tot[1] / 2;
   P->st = st;
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
+  P->cfg.orbits = opts_orbits(opts);
+  if (P->cfg.orbits < 0) {
+    delete P;
+    return EVOKE_EINVAL;
+  }
   // the largest component sizes the per-CTA maps of the root pass
   {
     u32* d = nullptr;
@@ -995,6 +1027,7 @@ int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* out) {
   out->root_threads = plan->rs.threads;
   out->root_ctas = plan->rs.ctas;
   out->root_ctas_max = plan->ctas_alloc;
+  out->orbits = plan->cfg.orbits;
   out->link_warps = (int32_t)plan->cfg.link_warps;
   return EVOKE_OK;
 }
@@ -1200,6 +1233,32 @@ int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n
     emit([&](long long* d) { copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E7, d, S); }, e7);
     emit([&](long long* d) { copy_i64_kernel<<<eb, 256, 0, st>>>(P->sa.E9, d, S); }, e9);
     if (tmp) cudaFreeAsync(tmp, st);
+    if (orig) cudaFreeAsync(orig, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = EVOKE_ECUDA;
+  }
+  plan_free(P);
+  return rc;
+}
+
+int evoke_edge_orbit_counts(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n,
+                            uint64_t m, int64_t* out, void* stream) {
+  if (!out && m) return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  evoke_plan* P = nullptr;
+  int rc = create_single(rowptr, colidx, n, m, nullptr, st, &P);
+  if (rc) return rc;
+  rc = run_once(P, nullptr, st);
+  const u64 S = P->g.S;
+  if (!rc && S) {
+    u32* orig = nullptr;
+    if (P->relabel && cudaMallocAsync(&orig, sizeof(u32) * S, st) != cudaSuccess) rc = EVOKE_ENOMEM;
+    if (!rc)
+      phase("edge_orbits", orig ? 2 : 1, st, [&] {
+        if (orig)
+          launch_orig_slot(P->in_rowptr, P->in_col, P->rl_old_of, P->rl_rowptr, P->rl_col, P->n,
+                           orig, st);
+        launch_edge_orbits12(P->g, P->sa, P->acc, reinterpret_cast<long long*>(out), orig, st);
+      });
     if (orig) cudaFreeAsync(orig, st);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = EVOKE_ECUDA;
   }

@@ -213,11 +213,14 @@ struct RootScratch {
   u64* cycles;   // optional [n]: cycles per root
   u64* cta_end;  // optional [ctas]: global timer (ns) when each CTA ran out of roots
   int ctas;
+  u32 smem_recs; // hot records of ids [0, smem_recs) kept in shared memory (set at launch)
 };
 size_t root_scratch_bytes(u32 map_n, int ctas);
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
+// four: the 4-vertex-orbit variant (wedges and C4(u) only)
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
-                           u32* pref, u32 pref_stride, cudaStream_t st);
+                           u32* pref, u32 pref_stride, bool four, cudaStream_t st);
+void root_configure();  // host-side set-up (kernel attributes)
 void link_configure();  // host-side set-up (kernel attributes)
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
                  cudaStream_t st);
@@ -246,8 +249,12 @@ void launch_tri_opp2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_
 void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);
 int upload_transform(const long long* A73x73);
+// orbits: 73 (out is n x 73) or 15 (the 4-vertex orbits 0..14 only, out n x 15)
 void launch_finalize(const Graph& g, const u64* acc, long long* out, const u32* old_of,
-                     cudaStream_t st);
+                     int orbits, cudaStream_t st);
+void launch_vsum2_four(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
+void launch_edge_orbits12(const Graph& g, const SlotArrays& sa, const u64* acc, long long* out,
+                          const u32* orig, cudaStream_t st);
 // learned work model
 int mlp_param_count();
 void launch_features(const Graph& g, const u64* acc, float* X, cudaStream_t st);

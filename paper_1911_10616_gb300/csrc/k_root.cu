@@ -15,6 +15,8 @@
 // shares of the chord ends;  3-paths ending at u -> 5-cycle credits and P;
 // (3) wedges again -> E5 = C4(u,v), orbit-49/62 shares of the centres, and
 // the 5-cycle credit of the wedge centre; map scan -> orbits 8, 36, 50, 51, 63.
+#include <cstdlib>
+
 #include "evoke_internal.cuh"
 
 namespace {
@@ -126,7 +128,8 @@ __device__ __forceinline__ u64 seg_sum(u32 key, u64 val, bool* is_tail) {
   return val;
 }
 
-template <int kThreads>
+// kFour: only what the 4-vertex orbits need (W -> C4(u) = DM8)
+template <int kThreads, bool kFour>
 __global__ void __launch_bounds__(kThreads)
 root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* pref_all,
             u32 pref_stride) {
@@ -138,6 +141,14 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
   MapCold* __restrict__ C = rs.cold + off;
   u32* __restrict__ touched = rs.touched + off;
   u32* __restrict__ jlist = rs.jlist + off;
+  // the records of the first rs.smem_recs ids live in shared memory instead
+  // (after the relabelling by decreasing degree these are the hubs, which
+  // most 2-hop walks reach); the global records of those ids stay unused
+  extern __shared__ __align__(16) unsigned char root_dyn_smem[];
+  MapHot* const s_hot = reinterpret_cast<MapHot*>(root_dyn_smem);
+  const u32 K = rs.smem_recs;
+  auto HP = [&](u32 lx) -> MapHot* { return lx < K ? s_hot + lx : H + lx; };
+  for (u32 i = threadIdx.x; i < K; i += blockDim.x) s_hot[i] = MapHot{};
   __shared__ u32 s_wpref[kThreads / 32][33];
   __shared__ u64 s_wsab[kThreads / 32][32];
   __shared__ u32 s_wsa[kThreads / 32][32];
@@ -180,7 +191,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     // phase 0: mark the neighbours, prefix of their degrees
     for (u32 i = threadIdx.x; i < du; i += blockDim.x) {
       const u32 v = g.col[ub + i];
-      H[v - cb].W = kFlag;
+      HP(v - cb)->W = kFlag;
       touched[atomicAdd(&s_nt, 1u)] = v;
     }
     const bool small = du + 1 <= kSmemPref;
@@ -214,7 +225,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       const u32 x = g.col[t];
       if (x == u) continue;
       const bool in_in = out && g.sin[t];  // u -> v <- x
-      const u64 old = atomicAdd(reinterpret_cast<u64*>(&H[x - cb].W),
+      const u64 old = atomicAdd(reinterpret_cast<u64*>(&HP(x - cb)->W),
                                 in_in ? 1ull : (1ull | (1ull << 32)));
       if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
     }
@@ -225,6 +236,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       tp = t;
     }
 
+    if constexpr (!kFour) {
     // phase 2a: diamonds.  Triangle (u,a,b) with a < b; every y in
     // N(a)^N(b) other than u closes a diamond with chord (a,b) and u, y off
     // the chord.  Each warp takes 32 triangle-list entries of u at a time and
@@ -275,10 +287,10 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
             }
             const u32 y = g.tlv[s_wsab[wid][lo] + (it - s_wpref[wid][lo])];
             if (y != u) {
-              const u64 wy2 = (u64)((long long)(H[y - cb].W & kW) - 2);
+              const u64 wy2 = (u64)((long long)(HP(y - cb)->W & kW) - 2);
               a63 += wy2;                 // DM63: sum over diamonds of W(u,y) - 2
               if (u < y) {
-                atomicAdd(&H[y - cb].D, 1u);  // D(u,y), needed for y > u only
+                atomicAdd(&HP(y - cb)->D, 1u);  // D(u,y), needed for y > u only
                 add = wy2;
                 key = lo;
               }
@@ -308,7 +320,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         const u64 old = atomicAdd(&C[x - cb].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
         if ((old >> 32) == 0) {
           jlist[atomicAdd(&s_nj, 1u)] = x;
-          atomicOr(&H[x - cb].W, kCold);
+          atomicOr(&HP(x - cb)->W, kCold);
         }
         const u32 mm = sa.Mmid[sk];
         if (mm) atomicAdd(&C[x - cb].X, mm);
@@ -328,20 +340,21 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         const u32 j = jlist[idx];
         const u64 ry = C[j - cb].RY;
         const u64 R = ry >> 32, Yj = ry & 0xffffffffull;
-        const bool jl = (H[j - cb].W & kFlag) != 0;
+        const bool jl = (HP(j - cb)->W & kFlag) != 0;
         const bool j_to_u = jl && prec(g.deg, j, u);
         u64 z = 0;
         for (u32 p = g.dag_ptr[j] + lane; p < g.dag_ptr[j + 1]; p += 32) {
           const u32 i = g.dag_col[p];
           if (i == u) continue;
-          const u32 wn = H[i - cb].Wn;
+          MapHot* hi = HP(i - cb);
+          const u32 wn = hi->Wn;
           if (!wn) continue;
           z += wn;
-          const u32 old = atomicAdd(&H[i - cb].P, (u32)R);
+          const u32 old = atomicAdd(&hi->P, (u32)R);
           if (old + (u32)R < old) *rs.overflow = 1;
           if (jl) {
             atomicAdd(&C[i - cb].Pjl, R);
-            if (!(H[i - cb].W & kCold)) atomicOr(&H[i - cb].W, kCold);
+            if (!(hi->W & kCold)) atomicOr(&hi->W, kCold);
           }
         }
         z = warp_sum(z);
@@ -378,7 +391,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (x == u) {
             valid = false;
           } else {
-            const MapHot h = H[x - cb];
+            const MapHot h = *HP(x - cb);
             const long long wx = h.W & kW;
             e5 = (u64)(wx - 1);
             a51 += ((u64)sa.T[t] - ((h.W & kFlag) ? 1 : 0)) * (u64)(wx - 1);
@@ -404,7 +417,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         const u32 j = g.dag_col[p];
         if (j == u) continue;
         u64 t = C[j - cb].Z;
-        if (H[j - cb].W & kFlag) {
+        if (HP(j - cb)->W & kFlag) {
           const u64 dpj = (u64)(g.dag_ptr[j + 1] - g.dag_ptr[j]) - (prec(g.deg, j, u) ? 1 : 0);
           t -= dpj;
         }
@@ -425,14 +438,26 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       tp = t;
     }
 
+    }  // !kFour
+
     // phase 3b: scan the map (orbits 8, 36, 50; the 5-cycle credits of the
     // path ends), reset it
-    {
+    if constexpr (kFour) {
+      u64 a8 = 0;
+      const u32 nt = s_nt;
+      for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
+        MapHot* hx = HP(touched[idx] - cb);
+        a8 += c2(hx->W & kW);
+        *hx = MapHot{};
+      }
+      a8 = block_sum(a8, s_red);
+      if (threadIdx.x == 0) acc[(u64)A_DM8 * n + u] = a8;
+    } else {
       u64 a8 = 0, a36 = 0, a50 = 0, a5 = 0;
       const u32 nt = s_nt;
       for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
         const u32 x = touched[idx];
-        const MapHot h = H[x - cb];
+        const MapHot h = *HP(x - cb);
         const long long w = h.W & kW;
         const u64 cw2 = c2(w);
         a8 += cw2;
@@ -453,7 +478,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
           if (ci) atomicAdd(&acc[(u64)A_C5 * n + x], ci);
           a5 += ci;
         }
-        H[x - cb] = MapHot{};
+        *HP(x - cb) = MapHot{};
       }
       a8 = block_sum(a8, s_red);
       if (threadIdx.x == 0) acc[(u64)A_DM8 * n + u] = a8;
@@ -768,14 +793,68 @@ void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st)
   sched_scatter_kernel<<<(g.n + 255) / 256, 256, 0, st>>>(work, g.n, rs.bucket_cnt, rs.order);
 }
 
+namespace {
+// Shared memory left for map records when `per_sm` CTAs of root_kernel<T, F>
+// share an SM; sets the kernel's dynamic shared-memory limit once.
+template <int T, bool F>
+size_t root_dyn_smem(int per_sm) {
+  static size_t static_smem = 0, per_sm_smem = 0, reserved = 0, optin = 0;
+  static bool ready = false;
+  if (!ready) {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, root_kernel<T, F>);
+    int dev = 0, a = 0, b = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&a, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&b, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    static_smem = fa.sharedSizeBytes;
+    per_sm_smem = (size_t)a;
+    reserved = (size_t)b;
+    optin = (size_t)c;
+    const size_t cap = optin > static_smem ? optin - static_smem : 0;
+    cudaFuncSetAttribute(root_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    cudaFuncSetAttribute(root_kernel<T, F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    ready = true;
+  }
+  if (per_sm < 1) per_sm = 1;
+  const size_t share = per_sm_smem / (size_t)per_sm;
+  if (share <= reserved + static_smem + 1024) return 0;
+  size_t dyn = share - reserved - static_smem;
+  if (dyn + static_smem > optin) dyn = optin - static_smem;
+  return dyn / 512 * 512;
+}
+}  // namespace
+
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
-                           u32* pref, u32 pref_stride, cudaStream_t st) {
+                           u32* pref, u32 pref_stride, bool four, cudaStream_t st) {
   if (!g.n) return;
   cudaMemsetAsync(rs.head, 0, sizeof(u32), st);
-  if (rs.threads == 256)
-    root_kernel<256><<<rs.ctas, 256, 0, st>>>(g, sa, acc, rs, pref, pref_stride);
-  else
-    root_kernel<512><<<rs.ctas, 512, 0, st>>>(g, sa, acc, rs, pref, pref_stride);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = (rs.ctas + sms - 1) / sms;
+  size_t dyn = rs.threads == 256 ? (four ? root_dyn_smem<256, true>(per_sm) : root_dyn_smem<256, false>(per_sm))
+                                 : (four ? root_dyn_smem<512, true>(per_sm) : root_dyn_smem<512, false>(per_sm));
+  u64 recs = dyn / sizeof(MapHot);
+  if (recs > rs.map_n) recs = rs.map_n;
+  if (getenv("EVOKE_ROOT_NO_SMEM_MAP")) recs = 0;
+  rs.smem_recs = (u32)recs;
+  dyn = (size_t)recs * sizeof(MapHot);
+  if (rs.threads == 256) {
+    if (four) root_kernel<256, true><<<rs.ctas, 256, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
+    else root_kernel<256, false><<<rs.ctas, 256, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
+  } else {
+    if (four) root_kernel<512, true><<<rs.ctas, 512, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
+    else root_kernel<512, false><<<rs.ctas, 512, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
+  }
+}
+
+void root_configure() {
+  root_dyn_smem<256, false>(4);
+  root_dyn_smem<512, false>(2);
+  root_dyn_smem<256, true>(4);
+  root_dyn_smem<512, true>(2);
 }
 
 void link_configure() {

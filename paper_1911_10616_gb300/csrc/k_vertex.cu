@@ -174,10 +174,13 @@ __constant__ unsigned short kNzCol[kMaxNz];
 __constant__ short kNzVal[kMaxNz];
 __constant__ unsigned short kRowStart[74];
 
+// kOrb = 73: all orbits; kOrb = 15: the 4-vertex orbits 0..14 only (A is
+// block diagonal by pattern size, so their rows of A^-1 stay inside 0..14)
+template <int kOrb>
 __global__ void __launch_bounds__(kFinalThreads)
 finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ out,
                 const u32* __restrict__ old_of) {
-  __shared__ long long s_out[kFinalThreads * 73];
+  __shared__ long long s_out[kFinalThreads * kOrb];
   const u32 n = g.n;
   const u32 u0 = blockIdx.x * kFinalThreads;
   const u32 u = u0 + threadIdx.x;
@@ -206,6 +209,7 @@ finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ ou
     M[12] = DM12;
     M[13] = DM13;
     M[14] = DM14;
+    if constexpr (kOrb == 73) {
     M[15] = a(A_S15) - DM5 - 2 * DM11 - 2 * DM8;
     M[16] = DM4 * sgn(d - 1) - DM10 - 2 * DM8;
     M[17] = c2u(DM1) - DM3 - DM6 - DM8 - DM10;
@@ -264,9 +268,10 @@ finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ ou
     M[70] = a(A_S70);
     M[71] = a(A_S71);
     M[72] = a(A_K5);
-    // induced counts: back substitution from orbit 72 down
-    long long* o = s_out + threadIdx.x * 73;
-    for (int i = 72; i >= 0; --i) {
+    }
+    // induced counts: back substitution from the last orbit down
+    long long* o = s_out + threadIdx.x * kOrb;
+    for (int i = kOrb - 1; i >= 0; --i) {
       u64 v = M[i];
       for (int k = kRowStart[i]; k < kRowStart[i + 1]; ++k)
         v -= (u64)(long long)kNzVal[k] * (u64)o[kNzCol[k]];
@@ -276,14 +281,39 @@ finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ ou
   __syncthreads();
   const u32 cnt = min((u32)kFinalThreads, n - u0);
   if (!old_of) {
-    long long* dst = out + (u64)u0 * 73;
-    for (u32 i = threadIdx.x; i < cnt * 73; i += kFinalThreads) dst[i] = s_out[i];
+    long long* dst = out + (u64)u0 * kOrb;
+    for (u32 i = threadIdx.x; i < cnt * kOrb; i += kFinalThreads) dst[i] = s_out[i];
   } else {  // relabelled graph: row of vertex u0 + r goes to its caller id
-    for (u32 i = threadIdx.x; i < cnt * 73; i += kFinalThreads) {
-      const u32 r = i / 73, k = i % 73;
-      out[(u64)old_of[u0 + r] * 73 + k] = s_out[i];
+    for (u32 i = threadIdx.x; i < cnt * kOrb; i += kFinalThreads) {
+      const u32 r = i / kOrb, k = i % kOrb;
+      out[(u64)old_of[u0 + r] * kOrb + k] = s_out[i];
     }
   }
+}
+
+// round 2 of the 4-vertex-orbit mode: DM4, DM9, DM12, DM14 only
+__global__ void vsum2_four_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
+  const u32 u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (u >= g.n) return;
+  const u32 n = g.n;
+  u64 s4 = 0, s9 = 0, k4 = 0;
+  for (u32 s = g.rowptr[u] + lane; s < g.rowptr[u + 1]; s += 32) {
+    const u32 v = g.col[s];
+    s4 += A(acc, A_DM1, n, v);
+    s9 += A(acc, A_T, n, v) - sa.T[s];
+    k4 += sa.K4[s];
+  }
+  s4 = warp_sum(s4);
+  s9 = warp_sum(s9);
+  k4 = warp_sum(k4);
+  if (lane) return;
+  const long long d = g.rowptr[u + 1] - g.rowptr[u];
+  const u64 T = A(acc, A_T, n, u);
+  acc[(u64)A_DM4 * n + u] = s4 - 2 * c2(d) - 2 * T;
+  acc[(u64)A_DM9 * n + u] = s9;
+  acc[(u64)A_DM12 * n + u] = A(acc, A_S12, n, u) >> 1;
+  acc[(u64)A_DM14 * n + u] = k4 / 3;
 }
 
 inline unsigned warp_blocks(u32 n) { return (unsigned)(((u64)n * 32 + 255) / 256); }
@@ -327,8 +357,57 @@ int upload_transform(const long long* A) {
 }
 
 void launch_finalize(const Graph& g, const u64* acc, long long* out, const u32* old_of,
-                     cudaStream_t st) {
+                     int orbits, cudaStream_t st) {
   if (!g.n) return;
-  finalize_kernel<<<(g.n + kFinalThreads - 1) / kFinalThreads, kFinalThreads, 0, st>>>(g, acc, out,
-                                                                                     old_of);
+  const unsigned blocks = (g.n + kFinalThreads - 1) / kFinalThreads;
+  if (orbits == 15)
+    finalize_kernel<15><<<blocks, kFinalThreads, 0, st>>>(g, acc, out, old_of);
+  else
+    finalize_kernel<73><<<blocks, kFinalThreads, 0, st>>>(g, acc, out, old_of);
+}
+
+void launch_vsum2_four(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {
+  if (!g.n) return;
+  vsum2_four_kernel<<<warp_blocks(g.n), 256, 0, st>>>(g, sa, acc);
+}
+
+// --- edge orbits of the 3- and 4-vertex patterns (Lem. 4edgeorbit) --------
+// One thread per slot s = (u,v); row s (or orig[s] for relabelled plans) of
+// `out` receives E0..E11 <u,v>, u on the side of the higher vertex orbit for
+// the asymmetric edge orbits (Fig. edge_orbits).  The five edge sums the
+// earlier passes keep per slot (T, E5 = C4(u,v), E7, E9, K4) are combined
+// with d(u), d(v), T(u) and DM1(u).
+__global__ void edge_orbit_kernel(Graph g, SlotArrays sa, const u64* __restrict__ acc,
+                                  long long* __restrict__ out, const u32* __restrict__ orig) {
+  const u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.S) return;
+  const u32 n = g.n;
+  const u32 v = g.col[s], u = g.col[g.rev[s]];
+  const long long du = g.deg[u], dv = g.deg[v];
+  const long long t = sa.T[s];
+  const u64 tu = acc[(u64)A_T * n + u], dm1 = acc[(u64)A_DM1 * n + u];
+  u64 e[12];
+  e[0] = (u64)(du - 1);
+  e[1] = (u64)t;
+  e[2] = dm1 - (u64)(dv - 1) - (u64)t;            // 3-paths v-u-x-y, u inner
+  e[3] = (u64)((du - 1) * (dv - 1) - t);           // 3-paths with (u,v) in the middle
+  e[4] = c2(du - 1);                               // 3-stars centred at u
+  e[5] = sa.E5[s];                                 // 4-cycles through (u,v)
+  e[6] = tu - (u64)t;                              // paws, u the centre, v the pendant
+  e[7] = sa.E7[s];                                 // paws with (u,v) opposite the centre
+  e[8] = (u64)(t * (du - 2));                      // paws, u the centre, v on the triangle
+  e[9] = sa.E9[s];                                 // diamonds, u a chord end, v a tip
+  e[10] = c2(t);                                   // diamonds with chord (u,v)
+  e[11] = sa.K4[s];                                // 4-cliques
+  const u64 row = orig ? (u64)orig[s] : s;
+  long long* o = out + row * 12;
+#pragma unroll
+  for (int i = 0; i < 12; i += 2)
+    *reinterpret_cast<longlong2*>(o + i) = make_longlong2((long long)e[i], (long long)e[i + 1]);
+}
+
+void launch_edge_orbits12(const Graph& g, const SlotArrays& sa, const u64* acc, long long* out,
+                          const u32* orig, cudaStream_t st) {
+  if (!g.S) return;
+  edge_orbit_kernel<<<(unsigned)((g.S + 255) / 256), 256, 0, st>>>(g, sa, acc, out, orig);
 }
