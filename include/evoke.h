@@ -49,6 +49,7 @@ extern "C" {
 #define EVOKE_ECUDA 5        /* a CUDA call or kernel launch failed */
 #define EVOKE_ETIMEOUT 6     /* a bounded device wait gave up */
 #define EVOKE_EOVERFLOW 7    /* an internal 32-bit count (3-paths per vertex pair) wrapped */
+#define EVOKE_EINCONSISTENT 8 /* counts whose orbits of one pattern disagree (totals) */
 
 typedef struct evoke_opts {
   int32_t validate;   /* nonzero: check the CSR invariants first (syncs the stream) */
@@ -58,6 +59,8 @@ typedef struct evoke_opts {
                          15: the 4-vertex orbits 0..14 only (Thm. 4orbit,
                          Lem. 4vertexorbit), out is int64[n*15] and the
                          5-vertex passes are skipped; other values: EVOKE_EINVAL */
+  int32_t noninduced; /* nonzero: write the non-induced counts DM (Sec. 2
+                         "Induced vs non-induced"; A^-1 of App. A not applied) */
 } evoke_opts;
 
 /*
@@ -246,6 +249,23 @@ int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n
  */
 int evoke_edge_orbit_counts(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n,
                             uint64_t m, int64_t* out, void* stream);
+
+/*
+ * evoke_graphlet_totals -- global pattern counts from per-vertex orbit
+ * counts: totals[j] = (sum over u of counts[u][o]) / |orbit o| for any
+ * orbit o of pattern H_j (each copy of H_j has |orbit o| vertices in o).
+ * Induced counts give induced copies, non-induced counts non-induced ones.
+ *   counts : device int64[n * orbits], as written by evoke_count_orbits /
+ *            evoke_count_batch / evoke_plan_execute (read only).
+ *   orbits : 73 (totals of H0..H29, 30 entries) or 15 (H0..H8, 9 entries).
+ *   totals : HOST int64[30] or int64[9] (written).
+ * Synchronises `stream`.  Errors: EVOKE_EINVAL (null pointers, orbits not
+ * 73 or 15), EVOKE_ENOMEM, EVOKE_ECUDA, EVOKE_EINCONSISTENT (a column sum
+ * is not a multiple of its orbit size, or two orbits of one pattern give
+ * different totals: not an orbit-count matrix; totals are still written).
+ */
+int evoke_graphlet_totals(const int64_t* counts, uint32_t n, int32_t orbits, int64_t* totals,
+                          void* stream);
 
 /*
  * evoke_orbit_matrix -- the library's matrix A of App. A (DM = A * DIM),

@@ -9,9 +9,10 @@ Public API (CUDA only; no CPU fallback):
     count_batch(rowptr_cat, colidx_cat, vtx_off, edge_off) -> counts of many graphs
     Plan.single / Plan.batch            -> sized plans: execute(), launch_graph()
     orbit_matrix()                      -> the 73x73 matrix A (DM = A DIM)
+    graphlet_totals(counts)             -> global pattern counts from orbit counts
 """
 from ._lib import (EvokeError, Plan, batch_to_device, build_dag, count_batch, count_orbits,
-                   edge_orbit_counts, edge_orbits, load, orbit_matrix, to_device, version)
+                   edge_orbit_counts, edge_orbits, graphlet_totals, load, orbit_matrix, to_device, version)
 
 __all__ = ["EvokeError", "Plan", "batch_to_device", "build_dag", "count_batch", "count_orbits",
-           "edge_orbit_counts", "edge_orbits", "load", "orbit_matrix", "to_device", "version"]
+           "edge_orbit_counts", "edge_orbits", "graphlet_totals", "load", "orbit_matrix", "to_device", "version"]

@@ -20,12 +20,13 @@ NORB = 73
 
 _ERRORS = {
     1: "EVOKE_EINVAL", 2: "EVOKE_ENOTSIMPLE", 3: "EVOKE_ERANGE", 4: "EVOKE_ENOMEM",
-    5: "EVOKE_ECUDA", 6: "EVOKE_ETIMEOUT", 7: "EVOKE_EOVERFLOW",
+    5: "EVOKE_ECUDA", 6: "EVOKE_ETIMEOUT", 7: "EVOKE_EOVERFLOW", 8: "EVOKE_EINCONSISTENT",
 }
 
 # exported symbols of include/evoke.h
 SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
            "evoke_build_dag_noalloc", "evoke_edge_orbits", "evoke_edge_orbit_counts",
+           "evoke_graphlet_totals",
            "evoke_orbit_matrix",
            "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
            "evoke_plan_launch_graph", "evoke_plan_execute_profiled", "evoke_plan_info", "evoke_plan_set_tuning",
@@ -57,7 +58,8 @@ class PlanStats(ctypes.Structure):
 
 class EvokeOpts(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("root_ctas", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("orbits", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("orbits", ctypes.c_int32),
+                ("noninduced", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -87,6 +89,9 @@ def load(build_if_missing: bool = True):
         lib.evoke_edge_orbits.restype = ctypes.c_int
         lib.evoke_edge_orbit_counts.argtypes = [vp, vp, u32, u64, vp, vp]
         lib.evoke_edge_orbit_counts.restype = ctypes.c_int
+        lib.evoke_graphlet_totals.argtypes = [vp, u32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int64), vp]
+        lib.evoke_graphlet_totals.restype = ctypes.c_int
         lib.evoke_orbit_matrix.argtypes = [ctypes.POINTER(ctypes.c_int64)]
         lib.evoke_orbit_matrix.restype = ctypes.c_int
         lib.evoke_strerror.argtypes = [ctypes.c_int]
@@ -171,9 +176,10 @@ def _orbits(orbits: int) -> int:
 
 
 def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = False,
-                 root_ctas: int = 0, stream=None, orbits: int = 73):
-    """Induced orbit counts, int64 tensor [n, orbits] on the graph's device
-    (orbits = 73: all; 15: the 4-vertex orbits 0..14 only)."""
+                 root_ctas: int = 0, stream=None, orbits: int = 73, induced: bool = True):
+    """Orbit counts, int64 tensor [n, orbits] on the graph's device (orbits =
+    73: all; 15: the 4-vertex orbits 0..14 only); induced=False gives the
+    non-induced counts DM."""
     import torch
     _check_graph(rowptr, colidx, n)
     k = _orbits(orbits)
@@ -181,7 +187,7 @@ def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = Fals
         out = torch.empty((n, k), dtype=torch.int64, device=rowptr.device)
     elif out.dtype != torch.int64 or out.numel() != n * k or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous int64 tensor with n*{k} entries")
-    opts = EvokeOpts(1 if validate else 0, int(root_ctas), 0, k)
+    opts = EvokeOpts(1 if validate else 0, int(root_ctas), 0, k, 0 if induced else 1)
     rc = load().evoke_count_orbits(_ptr(rowptr), _ptr(colidx), n, m, _ptr(out),
                                    ctypes.byref(opts), _stream_handle(stream))
     _check(rc, "evoke_count_orbits")
@@ -200,7 +206,7 @@ def batch_to_device(graphs, device="cuda"):
 
 
 def count_batch(rowptr_cat, colidx_cat, vtx_off, edge_off, out=None, validate: bool = False,
-                stream=None, orbits: int = 73):
+                stream=None, orbits: int = 73, induced: bool = True):
     """Induced orbit counts of a batch of graphs, int64 [sum n_g, orbits]."""
     import torch
     G = vtx_off.numel() - 1
@@ -208,7 +214,7 @@ def count_batch(rowptr_cat, colidx_cat, vtx_off, edge_off, out=None, validate: b
     k = _orbits(orbits)
     if out is None:
         out = torch.empty((N, k), dtype=torch.int64, device=vtx_off.device)
-    opts = EvokeOpts(1 if validate else 0, 0, 0, k)
+    opts = EvokeOpts(1 if validate else 0, 0, 0, k, 0 if induced else 1)
     rc = load().evoke_count_batch(_ptr(rowptr_cat), _ptr(colidx_cat), _ptr(vtx_off),
                                   _ptr(edge_off), G, _ptr(out), ctypes.byref(opts),
                                   _stream_handle(stream))
@@ -228,10 +234,10 @@ class Plan:
 
     @classmethod
     def single(cls, rowptr, colidx, n: int, m: int, validate: bool = False, stream=None,
-               orbits: int = 73):
+               orbits: int = 73, induced: bool = True):
         _check_graph(rowptr, colidx, n)
         h = ctypes.c_void_p()
-        opts = EvokeOpts(1 if validate else 0, 0, 0, _orbits(orbits))
+        opts = EvokeOpts(1 if validate else 0, 0, 0, _orbits(orbits), 0 if induced else 1)
         _check(load().evoke_plan_create(_ptr(rowptr), _ptr(colidx), n, m, ctypes.byref(opts),
                                         _stream_handle(stream), ctypes.byref(h)),
                "evoke_plan_create")
@@ -239,9 +245,9 @@ class Plan:
 
     @classmethod
     def batch(cls, rowptr_cat, colidx_cat, vtx_off, edge_off, validate: bool = False,
-              stream=None, orbits: int = 73):
+              stream=None, orbits: int = 73, induced: bool = True):
         h = ctypes.c_void_p()
-        opts = EvokeOpts(1 if validate else 0, 0, 0, _orbits(orbits))
+        opts = EvokeOpts(1 if validate else 0, 0, 0, _orbits(orbits), 0 if induced else 1)
         G = vtx_off.numel() - 1
         _check(load().evoke_plan_create_batch(_ptr(rowptr_cat), _ptr(colidx_cat), _ptr(vtx_off),
                                               _ptr(edge_off), G, ctypes.byref(opts),
@@ -341,6 +347,20 @@ def edge_orbit_counts(rowptr, colidx, n: int, m: int, stream=None):
                                         _stream_handle(stream))
     _check(rc, "evoke_edge_orbit_counts")
     return out
+
+
+def graphlet_totals(counts, stream=None) -> np.ndarray:
+    """Global pattern counts from per-vertex orbit counts (int64 CUDA tensor
+    [n, 73] or [n, 15]): int64 array of 30 (H0..H29) or 9 (H0..H8) totals."""
+    k = _orbits(int(counts.shape[1]) if counts.dim() == 2 else 0)
+    if not counts.is_contiguous():
+        raise ValueError("counts must be contiguous")
+    n = int(counts.shape[0])
+    out = (ctypes.c_int64 * (30 if k == 73 else 9))()
+    rc = load().evoke_graphlet_totals(_ptr(counts) if n else None, n, k, out,
+                                      _stream_handle(stream))
+    _check(rc, "evoke_graphlet_totals")
+    return np.array(out[:], dtype=np.int64)
 
 
 def build_dag(rowptr, colidx, n: int, m: int, stream=None):

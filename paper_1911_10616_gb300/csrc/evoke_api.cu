@@ -90,6 +90,8 @@ bool spans_connected(Adj m, int k) {
 struct Derived {
   bool ok = false;
   long long A[73 * 73] = {};
+  int orbit_pattern[73] = {};  // pattern owning each orbit
+  int orbit_size[73] = {};     // vertices of the pattern in the orbit
 };
 
 Derived derive() {
@@ -115,8 +117,11 @@ Derived derive() {
         }
       } while (std::next_permutation(p, p + P.k));
     }
-    for (int a = 0; a < P.k; ++a)
+    for (int a = 0; a < P.k; ++a) {
       if (full_orb[j][a] < 0) return out;
+      out.orbit_pattern[full_orb[j][a]] = j;
+      out.orbit_size[full_orb[j][a]]++;
+    }
   }
   // A: connected spanning edge subsets of each pattern
   for (int j = 0; j < 30; ++j) {
@@ -351,6 +356,7 @@ struct Config {
   int root_ctas = 0;      // 0: 2 per SM (512 threads) / 4 per SM (256)
   u32 link_warps = 0;     // 0: 64 per SM
   int orbits = 73;        // 73, or 15: the 4-vertex orbits only
+  bool induced = true;    // false: write the non-induced counts DM
 };
 
 // evoke_opts.orbits: 0 or 73 -> all orbits, 15 -> orbits 0..14; else -1
@@ -733,7 +739,8 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
   }
   if (out)
     run("finalize", nl, [&] {
-      launch_finalize(g, acc, out, P->relabel ? P->rl_old_of : nullptr, P->cfg.orbits, st);
+      launch_finalize(g, acc, out, P->relabel ? P->rl_old_of : nullptr, P->cfg.orbits,
+                      P->cfg.induced, st);
     });
 }
 
@@ -789,6 +796,7 @@ int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, ui
   P->st = st;
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
   P->cfg.orbits = opts_orbits(opts);
+  P->cfg.induced = !(opts && opts->noninduced);
   if (P->cfg.orbits < 0) {
     plan_free(P);
     return EVOKE_EINVAL;
@@ -880,6 +888,7 @@ const char* evoke_strerror(int code) {
     case EVOKE_ECUDA: return "CUDA error";
     case EVOKE_ETIMEOUT: return "bounded device wait timed out";
     case EVOKE_EOVERFLOW: return "count overflow";
+    case EVOKE_EINCONSISTENT: return "orbit counts of one pattern disagree";
     default: return "unknown status";
   }
 }
@@ -930,6 +939,7 @@ int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_c
   P->st = st;
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
   P->cfg.orbits = opts_orbits(opts);
+  P->cfg.induced = !(opts && opts->noninduced);
   if (P->cfg.orbits < 0) {
     delete P;
     return EVOKE_EINVAL;
@@ -1263,6 +1273,49 @@ int evoke_edge_orbit_counts(const uint32_t* rowptr, const uint32_t* colidx, uint
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = EVOKE_ECUDA;
   }
   plan_free(P);
+  return rc;
+}
+
+int evoke_graphlet_totals(const int64_t* counts, uint32_t n, int32_t orbits, int64_t* totals,
+                          void* stream) {
+  if ((n && !counts) || !totals || (orbits != 73 && orbits != 15)) return EVOKE_EINVAL;
+  const Derived& d = derived();
+  if (!d.ok) return EVOKE_ECUDA;
+  const int np = orbits == 73 ? 30 : 9;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  u64 sums[73] = {};
+  if (n) {
+    u64* dsum = nullptr;
+    if (cudaMallocAsync(&dsum, sizeof(u64) * orbits, st) != cudaSuccess) return EVOKE_ENOMEM;
+    cudaMemsetAsync(dsum, 0, sizeof(u64) * orbits, st);
+    launch_column_sums(reinterpret_cast<const long long*>(counts), n, orbits, dsum,
+                       sm_count_cached(), st);
+    {
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      g_launches += 1;
+    }
+    cudaMemcpyAsync(sums, dsum, sizeof(u64) * orbits, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(dsum, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      return EVOKE_ECUDA;
+  }
+  // each copy of pattern j puts orbit_size[o] of its vertices in orbit o, so
+  // every orbit of j must give the same quotient
+  int rc = EVOKE_OK;
+  for (int j = 0; j < np; ++j) {
+    bool first = true;
+    long long t = 0;
+    for (int o = 0; o < orbits; ++o) {
+      if (d.orbit_pattern[o] != j) continue;
+      const u64 sz = (u64)d.orbit_size[o];
+      if (sums[o] % sz) rc = EVOKE_EINCONSISTENT;
+      const long long q = (long long)(sums[o] / sz);
+      if (first) t = q;
+      else if (q != t) rc = EVOKE_EINCONSISTENT;
+      first = false;
+    }
+    totals[j] = t;
+  }
   return rc;
 }
 

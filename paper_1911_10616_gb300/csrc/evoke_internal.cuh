@@ -250,8 +250,11 @@ void launch_vsum2(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t s
 void launch_vsum3(const Graph& g, u64* acc, cudaStream_t st);
 int upload_transform(const long long* A73x73);
 // orbits: 73 (out is n x 73) or 15 (the 4-vertex orbits 0..14 only, out n x 15)
+// induced = false writes the non-induced counts DM (A^-1 not applied)
 void launch_finalize(const Graph& g, const u64* acc, long long* out, const u32* old_of,
-                     int orbits, cudaStream_t st);
+                     int orbits, bool induced, cudaStream_t st);
+void launch_column_sums(const long long* counts, u64 rows, int K, u64* sums, int sms,
+                        cudaStream_t st);
 void launch_vsum2_four(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st);
 void launch_edge_orbits12(const Graph& g, const SlotArrays& sa, const u64* acc, long long* out,
                           const u32* orig, cudaStream_t st);

@@ -176,10 +176,11 @@ __constant__ unsigned short kRowStart[74];
 
 // kOrb = 73: all orbits; kOrb = 15: the 4-vertex orbits 0..14 only (A is
 // block diagonal by pattern size, so their rows of A^-1 stay inside 0..14)
+// induced = false: the non-induced counts DM themselves (no A^-1).
 template <int kOrb>
 __global__ void __launch_bounds__(kFinalThreads)
 finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ out,
-                const u32* __restrict__ old_of) {
+                const u32* __restrict__ old_of, bool induced) {
   __shared__ long long s_out[kFinalThreads * kOrb];
   const u32 n = g.n;
   const u32 u0 = blockIdx.x * kFinalThreads;
@@ -273,8 +274,9 @@ finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ ou
     long long* o = s_out + threadIdx.x * kOrb;
     for (int i = kOrb - 1; i >= 0; --i) {
       u64 v = M[i];
-      for (int k = kRowStart[i]; k < kRowStart[i + 1]; ++k)
-        v -= (u64)(long long)kNzVal[k] * (u64)o[kNzCol[k]];
+      if (induced)
+        for (int k = kRowStart[i]; k < kRowStart[i + 1]; ++k)
+          v -= (u64)(long long)kNzVal[k] * (u64)o[kNzCol[k]];
       o[i] = (long long)v;
     }
   }
@@ -357,13 +359,37 @@ int upload_transform(const long long* A) {
 }
 
 void launch_finalize(const Graph& g, const u64* acc, long long* out, const u32* old_of,
-                     int orbits, cudaStream_t st) {
+                     int orbits, bool induced, cudaStream_t st) {
   if (!g.n) return;
   const unsigned blocks = (g.n + kFinalThreads - 1) / kFinalThreads;
   if (orbits == 15)
-    finalize_kernel<15><<<blocks, kFinalThreads, 0, st>>>(g, acc, out, old_of);
+    finalize_kernel<15><<<blocks, kFinalThreads, 0, st>>>(g, acc, out, old_of, induced);
   else
-    finalize_kernel<73><<<blocks, kFinalThreads, 0, st>>>(g, acc, out, old_of);
+    finalize_kernel<73><<<blocks, kFinalThreads, 0, st>>>(g, acc, out, old_of, induced);
+}
+
+// Column sums of an int64[rows x K] count matrix (K = 73 or 15), wrapping
+// u64.  Every block has a multiple of K threads and so does the grid, so a
+// grid-stride walk keeps each thread on one column.
+__global__ void column_sums_kernel(const long long* __restrict__ counts, u64 total, int K,
+                                   u64* __restrict__ sums) {
+  __shared__ u64 s[73];
+  if (threadIdx.x < (unsigned)K) s[threadIdx.x] = 0;
+  __syncthreads();
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  u64 a = 0;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+    a += (u64)counts[i];
+  if (a) atomicAdd(&s[threadIdx.x % K], a);
+  __syncthreads();
+  if (threadIdx.x < (unsigned)K && s[threadIdx.x]) atomicAdd(&sums[threadIdx.x], s[threadIdx.x]);
+}
+
+void launch_column_sums(const long long* counts, u64 rows, int K, u64* sums, int sms,
+                        cudaStream_t st) {
+  if (!rows) return;
+  const int threads = 1024 / K * K;
+  column_sums_kernel<<<2 * sms, threads, 0, st>>>(counts, rows * (u64)K, K, sums);
 }
 
 void launch_vsum2_four(const Graph& g, const SlotArrays& sa, u64* acc, cudaStream_t st) {

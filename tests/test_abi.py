@@ -43,3 +43,17 @@ def test_null_arguments_rejected_without_gpu_work():
     lib = _lib.load()
     assert lib.evoke_orbit_matrix(None) == 1
     assert lib.evoke_count_orbits(None, None, 5, 3, None, None, None) == 1
+
+
+def test_totals_argument_checks_and_empty_input_without_gpu():
+    from paper_1911_10616_gb300 import _lib
+    lib = _lib.load()
+    buf = (ctypes.c_int64 * 30)()
+    assert lib.evoke_graphlet_totals(None, 0, 20, buf, None) == 1   # orbits not 73 / 15
+    assert lib.evoke_graphlet_totals(None, 5, 73, buf, None) == 1   # counts missing
+    assert lib.evoke_graphlet_totals(None, 0, 73, None, None) == 1  # totals missing
+    for k in range(30):
+        buf[k] = -1
+    assert lib.evoke_graphlet_totals(None, 0, 73, buf, None) == 0   # no vertices: all zero
+    assert list(buf) == [0] * 30
+    assert lib.evoke_strerror(8).startswith(b"orbit counts")
