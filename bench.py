@@ -403,7 +403,7 @@ def run_batch(args, rank, world, dist, barrier):
 
     # autotune the per-root pass: threads per CTA and persistent CTAs
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    cands = [(512, 2 * sms), (256, 4 * sms), (512, sms), (256, 2 * sms)]
+    cands = [(512, 2 * sms), (256, 4 * sms), (128, 8 * sms), (64, 16 * sms), (64, 12 * sms)]
     tune = []
     for th, ct in cands:
         if ct > info["root_ctas_max"]:

@@ -141,8 +141,9 @@ int evoke_plan_launch_graph(evoke_plan* plan, int64_t* out, void* stream);
  * (when evoke_profile_enable is on); same kernels, same results. */
 int evoke_plan_execute_profiled(evoke_plan* plan, int64_t* out, void* stream);
 int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* stats);
-/* Autotuning hook: threads per CTA (256 or 512) and the number of persistent
- * CTAs of the per-root pass, at most the number the plan was created with. */
+/* Autotuning hook: threads per CTA (64, 128, 256 or 512; the narrow shapes
+ * suit batches of small graphs) and the number of persistent CTAs of the
+ * per-root pass, at most root_ctas_max of evoke_plan_info. */
 int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_ctas);
 int evoke_plan_destroy(evoke_plan* plan);
 

@@ -451,16 +451,21 @@ int check_csr(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64
 
 void apply_config(evoke_plan* P, u32 map_n) {
   const int sms = sm_count_cached();
-  P->rs.threads = P->cfg.root_threads == 256 ? 256 : 512;
-  P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (P->rs.threads == 256 ? 4 : 2);
-  // maps for up to 4 CTAs per SM when that is cheap, so that tuning can
-  // raise the CTA count later
+  const int t = P->cfg.root_threads;
+  P->rs.threads = (t == 64 || t == 128 || t == 256) ? t : 512;
+  P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (1024 / P->rs.threads);
+  // maps for up to 16 (small maps) or 4 CTAs per SM when that is cheap, so
+  // that tuning can raise the CTA count later
   const size_t per_cta = (size_t)map_n * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32));
   P->ctas_alloc = P->rs.ctas;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)4 << 30;
   const size_t budget = std::min<size_t>(free_b / 3, (size_t)64 << 30);
-  if ((size_t)sms * 4 * per_cta <= budget) P->ctas_alloc = std::max(P->ctas_alloc, sms * 4);
+  for (int per_sm : {16, 8, 4})
+    if ((size_t)sms * per_sm * per_cta <= budget) {
+      P->ctas_alloc = std::max(P->ctas_alloc, sms * per_sm);
+      break;
+    }
 }
 
 // the CSR invariants of the caller's graph (simple, symmetric, sorted rows)
@@ -1043,8 +1048,10 @@ int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* out) {
 }
 
 int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_ctas) {
-  if (!plan || (root_threads != 256 && root_threads != 512) || root_ctas <= 0) return EVOKE_EINVAL;
-  const int per_sm_max = root_threads == 256 ? 4 : 2;
+  if (!plan || root_ctas <= 0 ||
+      (root_threads != 64 && root_threads != 128 && root_threads != 256 && root_threads != 512))
+    return EVOKE_EINVAL;
+  const int per_sm_max = 2048 / root_threads;
   if (root_ctas > sm_count_cached() * per_sm_max * 4) return EVOKE_ERANGE;
   // the per-CTA maps were sized when the plan was created
   if (root_ctas > plan->ctas_alloc) return EVOKE_ERANGE;

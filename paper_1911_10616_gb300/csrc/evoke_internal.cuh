@@ -202,7 +202,7 @@ struct RootScratch {
   int* overflow; // set if a 32-bit 3-path count would wrap
   const u32* comp_base;  // optional [n]: first id of each vertex's component (batches)
   u32 map_n;     // records per CTA: n, or the largest component of a batch
-  int threads;   // 256 or 512 threads per CTA
+  int threads;   // 64, 128, 256 or 512 threads per CTA
   u32* touched;  // per CTA: n, ids touched by the current root
   u32* jlist;    // per CTA: n, middle vertices of the current root's 3-paths
   u32* order;    // n: roots in schedule order

@@ -108,7 +108,10 @@ __device__ void neighbour_degree_prefix(const Graph& g, u32 ub, u32 du, u32* pre
   __syncthreads();
 }
 
-constexpr u32 kSmemPref = 2048;  // neighbour-degree prefix kept in shared memory up to here
+// neighbour-degree prefix kept in shared memory for roots of degree below
+// this (smaller for the narrow CTAs used on batches of small graphs)
+template <int kThreads>
+constexpr u32 smem_pref_cap() { return kThreads >= 256 ? 2048u : 512u; }
 
 // per-warp segmented sum over runs of equal `key` (non-decreasing across the
 // lanes, 0xffffffff for idle lanes); returns the run total on the run's last
@@ -153,6 +156,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
   __shared__ u64 s_wsab[kThreads / 32][32];
   __shared__ u32 s_wsa[kThreads / 32][32];
   __shared__ u32 s_wsb[kThreads / 32][32];
+  constexpr u32 kSmemPref = smem_pref_cap<kThreads>();
   __shared__ u32 s_pref[kSmemPref + 1];
   __shared__ u32 s_nrp[kSmemPref];            // rowptr of each neighbour (small roots)
   __shared__ unsigned char s_nout[kSmemPref];  // u -> neighbour in the DAG
@@ -814,7 +818,6 @@ size_t root_dyn_smem(int per_sm) {
     optin = (size_t)c;
     const size_t cap = optin > static_smem ? optin - static_smem : 0;
     cudaFuncSetAttribute(root_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
-    cudaFuncSetAttribute(root_kernel<T, F>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     ready = true;
   }
   if (per_sm < 1) per_sm = 1;
@@ -834,25 +837,47 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = (rs.ctas + sms - 1) / sms;
-  size_t dyn = rs.threads == 256 ? (four ? root_dyn_smem<256, true>(per_sm) : root_dyn_smem<256, false>(per_sm))
-                                 : (four ? root_dyn_smem<512, true>(per_sm) : root_dyn_smem<512, false>(per_sm));
+  size_t dyn = 0;
+  switch (rs.threads) {
+    case 64: dyn = four ? root_dyn_smem<64, true>(per_sm) : root_dyn_smem<64, false>(per_sm); break;
+    case 128: dyn = four ? root_dyn_smem<128, true>(per_sm) : root_dyn_smem<128, false>(per_sm); break;
+    case 256: dyn = four ? root_dyn_smem<256, true>(per_sm) : root_dyn_smem<256, false>(per_sm); break;
+    default: dyn = four ? root_dyn_smem<512, true>(per_sm) : root_dyn_smem<512, false>(per_sm);
+  }
   u64 recs = dyn / sizeof(MapHot);
+  // more records than this cost the root pass more L1 cache than they save
+  // in map traffic (measured on the 1M-vertex Chung-Lu graph: 3,072 records
+  // per 512-thread CTA, 512 per 256-thread CTA)
+  const u64 cap = rs.threads == 512 ? 3072 : rs.threads == 256 ? 512 : recs;
+  if (recs > cap) recs = cap;
   if (recs > rs.map_n) recs = rs.map_n;
-  if (getenv("EVOKE_ROOT_NO_SMEM_MAP")) recs = 0;
+  if (const char* e = getenv("EVOKE_ROOT_SMEM_RECS")) {
+    const long long r = atoll(e);
+    if (r >= 0 && (u64)r < recs) recs = (u64)r;
+  }
   rs.smem_recs = (u32)recs;
   dyn = (size_t)recs * sizeof(MapHot);
-  if (rs.threads == 256) {
-    if (four) root_kernel<256, true><<<rs.ctas, 256, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
-    else root_kernel<256, false><<<rs.ctas, 256, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
-  } else {
-    if (four) root_kernel<512, true><<<rs.ctas, 512, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
-    else root_kernel<512, false><<<rs.ctas, 512, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
+#define EVOKE_ROOT_LAUNCH(T)                                                               \
+  do {                                                                                     \
+    if (four) root_kernel<T, true><<<rs.ctas, T, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); \
+    else root_kernel<T, false><<<rs.ctas, T, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);     \
+  } while (0)
+  switch (rs.threads) {
+    case 64: EVOKE_ROOT_LAUNCH(64); break;
+    case 128: EVOKE_ROOT_LAUNCH(128); break;
+    case 256: EVOKE_ROOT_LAUNCH(256); break;
+    default: EVOKE_ROOT_LAUNCH(512);
   }
+#undef EVOKE_ROOT_LAUNCH
 }
 
 void root_configure() {
+  root_dyn_smem<64, false>(16);
+  root_dyn_smem<128, false>(8);
   root_dyn_smem<256, false>(4);
   root_dyn_smem<512, false>(2);
+  root_dyn_smem<64, true>(16);
+  root_dyn_smem<128, true>(8);
   root_dyn_smem<256, true>(4);
   root_dyn_smem<512, true>(2);
 }

@@ -70,11 +70,12 @@ def test_totals_closed_forms(ev):
     paths = {j for j, (k, e) in enumerate(pats)
              if len(e) == k - 1 and max(np.bincount(np.ravel(e), minlength=k)) <= 2}
     assert np.array_equal(ind, np.array([9 if j in paths else 0 for j in range(30)]))
-    # star with 8 leaves: induced stars with 1..4 leaves
+    # star with L leaves: induced stars with 1..4 leaves
     g = gg.star(9)
+    leaves = g.m
     rp, col = ev.to_device(g)
     ind = ev.graphlet_totals(ev.count_orbits(rp, col, g.n, g.m))
-    stars = {j: comb(8, k - 1) for j, (k, e) in enumerate(pats)
+    stars = {j: comb(leaves, k - 1) for j, (k, e) in enumerate(pats)
              if len(e) == k - 1 and max(np.bincount(np.ravel(e), minlength=k)) == k - 1}
     assert np.array_equal(ind, np.array([stars.get(j, 0) for j in range(30)]))
     four = ev.graphlet_totals(ev.count_orbits(rp, col, g.n, g.m, orbits=15))
