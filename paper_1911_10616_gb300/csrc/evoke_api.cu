@@ -456,7 +456,8 @@ void apply_config(evoke_plan* P, u32 map_n) {
   P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (1024 / P->rs.threads);
   // maps for up to 16 (small maps) or 4 CTAs per SM when that is cheap, so
   // that tuning can raise the CTA count later
-  const size_t per_cta = (size_t)map_n * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32));
+  const size_t per_cta =
+      (size_t)root_map_stride(map_n) * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32));
   P->ctas_alloc = P->rs.ctas;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)4 << 30;
@@ -626,7 +627,7 @@ int plan_stage2(evoke_plan* P) {
     return e && *e && *e != '0';
   }();
   size_t bytes = 2 * sz<u32>(P->ntri_entries) + 9 * sz<u64>(S) + 2 * sz<u32>(S) + sz<u64>(8) +
-                 sz<u64>((size_t)NACC * n) + root_scratch_bytes(map_n, ctas) + 256 * 8 +
+                 sz<u64>((size_t)NACC * n) + root_scratch_bytes(root_map_stride(map_n), ctas) + 256 * 8 +
                  sz<u32>(n) + sz<u32>(256) + sz<u32>(4) +
                  sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * 2 * dmax);
   if (cudaMallocAsync(&P->block2, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
@@ -649,12 +650,13 @@ int plan_stage2(evoke_plan* P) {
   P->acc = ar.take<u64>((size_t)NACC * n);
   RootScratch& rs = P->rs;
   rs.map_n = map_n;
+  rs.map_stride = root_map_stride(map_n);
   rs.comp_base = P->batch ? P->comp_base : nullptr;
-  rs.hot = ar.take<MapHot>((size_t)ctas * map_n);
-  rs.cold = ar.take<MapCold>((size_t)ctas * map_n);
+  rs.hot = ar.take<MapHot>((size_t)ctas * rs.map_stride);
+  rs.cold = ar.take<MapCold>((size_t)ctas * rs.map_stride);
   rs.overflow = P->status + 1;
-  rs.touched = ar.take<u32>((size_t)ctas * map_n);
-  rs.jlist = ar.take<u32>((size_t)ctas * map_n);
+  rs.touched = ar.take<u32>((size_t)ctas * rs.map_stride);
+  rs.jlist = ar.take<u32>((size_t)ctas * rs.map_stride);
   rs.order = ar.take<u32>(n);
   rs.bucket_cnt = ar.take<u32>(256);
   rs.head = ar.take<u32>(4);

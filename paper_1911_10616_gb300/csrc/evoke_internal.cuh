@@ -202,6 +202,7 @@ struct RootScratch {
   int* overflow; // set if a 32-bit 3-path count would wrap
   const u32* comp_base;  // optional [n]: first id of each vertex's component (batches)
   u32 map_n;     // records per CTA: n, or the largest component of a batch
+  u32 map_stride;  // records between two CTAs' maps (root_map_stride(map_n))
   int threads;   // 64, 128, 256 or 512 threads per CTA
   u32* touched;  // per CTA: n, ids touched by the current root
   u32* jlist;    // per CTA: n, middle vertices of the current root's 3-paths
@@ -215,7 +216,11 @@ struct RootScratch {
   int ctas;
   u32 smem_recs; // hot records of ids [0, smem_recs) kept in shared memory (set at launch)
 };
-size_t root_scratch_bytes(u32 map_n, int ctas);
+// per-CTA record stride: at least map_n, an odd number of 128-byte lines of
+// hot records, so that the CTAs' records of one vertex do not sit a power
+// of two apart (and on the same L2 slice)
+u32 root_map_stride(u32 map_n);
+size_t root_scratch_bytes(u32 map_stride, int ctas);
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
 // four: the 4-vertex-orbit variant (wedges and C4(u) only)
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,

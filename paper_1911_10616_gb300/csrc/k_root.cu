@@ -139,7 +139,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
   constexpr u32 kCold = 0x40000000u;  // W bit 30: the cold record is in use
   constexpr u32 kW = 0x3fffffffu;
   const u32 n = g.n;
-  const u64 off = (u64)blockIdx.x * rs.map_n;
+  const u64 off = (u64)blockIdx.x * rs.map_stride;
   MapHot* __restrict__ H = rs.hot + off;
   MapCold* __restrict__ C = rs.cold + off;
   u32* __restrict__ touched = rs.touched + off;
@@ -278,16 +278,20 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
         s_wsb[wid][lane] = sb;
         __syncwarp();
         const u32 tot = s_wpref[wid][32];
+        u32 lo = 0;  // chord list of entry `it`; non-decreasing as `it` grows
         for (u32 it0 = 0; it0 < tot; it0 += 32) {
           const u32 it = it0 + lane;
           u32 key = 0xffffffffu;
           u64 add = 0;
           if (it < tot) {
-            u32 lo = 0, hi = 32;
-            while (hi - lo > 1) {
-              const u32 mid = (lo + hi) >> 1;
-              if (s_wpref[wid][mid] <= it) lo = mid;
-              else hi = mid;
+            if (s_wpref[wid][lo + 1] <= it) {
+              u32 hi = 32;
+              ++lo;
+              while (hi - lo > 1) {
+                const u32 mid = (lo + hi) >> 1;
+                if (s_wpref[wid][mid] <= it) lo = mid;
+                else hi = mid;
+              }
             }
             const u32 y = g.tlv[s_wsab[wid][lo] + (it - s_wpref[wid][lo])];
             if (y != u) {
@@ -596,12 +600,16 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
       s_start[wid][lane] = st0;
       __syncwarp();
       const u32 tot = s_pref[wid][32];
+      u32 l2 = 0;  // list of entry `it`; non-decreasing as `it` grows
       for (u32 it = lane; it < tot; it += 32) {
-        u32 l2 = 0, h2 = 32;
-        while (h2 - l2 > 1) {
-          const u32 mid = (l2 + h2) >> 1;
-          if (s_pref[wid][mid] <= it) l2 = mid;
-          else h2 = mid;
+        if (s_pref[wid][l2 + 1] <= it) {
+          u32 h2 = 32;
+          ++l2;
+          while (h2 - l2 > 1) {
+            const u32 mid = (l2 + h2) >> 1;
+            if (s_pref[wid][mid] <= it) l2 = mid;
+            else h2 = mid;
+          }
         }
         const u32 pc = g.tl[s_start[wid][l2] + (it - s_pref[wid][l2])] - ub;
         u32 old;
@@ -784,8 +792,14 @@ k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
 
 }  // namespace
 
-size_t root_scratch_bytes(u32 map_n, int ctas) {
-  return (size_t)ctas * map_n * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32)) + 16 * 256;
+u32 root_map_stride(u32 map_n) {
+  const u64 lines = ((u64)map_n + 7) / 8 + 3;  // 8 hot records per 128-byte line
+  return (u32)((lines | 1) * 8);
+}
+
+size_t root_scratch_bytes(u32 map_stride, int ctas) {
+  return (size_t)ctas * map_stride * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32)) +
+         16 * 256;
 }
 
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st) {
