@@ -57,8 +57,10 @@ typedef struct evoke_opts {
   int32_t schedule;   /* 0 = degree-bucket schedule (decreasing wedge work) */
   int32_t orbits;     /* 0 or 73: all 73 orbits, out is int64[n*73];
                          15: the 4-vertex orbits 0..14 only (Thm. 4orbit,
-                         Lem. 4vertexorbit), out is int64[n*15] and the
-                         5-vertex passes are skipped; other values: EVOKE_EINVAL */
+                         Lem. 4vertexorbit), out is int64[n*15]; the passes
+                         that feed only 5-vertex orbits (wheels, 5-cliques,
+                         their neighbour sums) are skipped; other values:
+                         EVOKE_EINVAL */
   int32_t noninduced; /* nonzero: write the non-induced counts DM (Sec. 2
                          "Induced vs non-induced"; A^-1 of App. A not applied) */
 } evoke_opts;

@@ -715,7 +715,7 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
   run("tri_scan", S ? 3 : 0, [&] { launch_scan_u32_to_u64(sa.T, g.tl_ptr, S, P->scan_tmp, st); });
   const bool four = P->cfg.orbits == 15;
   run("tri_fill", sl, [&] { launch_tri_fill(g, sa.T, st); });
-  if (!four) run("tri_edge", sl, [&] { launch_tri_edge(g, sa, st); });
+  run("tri_edge", sl, [&] { launch_tri_edge(g, sa, st); });
   run("vsum1", nl, [&] { launch_vsum1(g, sa, acc, st); });
   run("tri_opp1", nl, [&] { launch_tri_opp1(g, sa, acc, st); });
   run("k4", (P->ntri_entries ? 1 : 0) + sl, [&] { launch_k4_known(g, sa, acc, P->ntri_entries, st); });
@@ -731,7 +731,7 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
     run("schedule", 3 * nl, [&] { launch_schedule(g, acc, P->rs, st); });
   }
   run("root", nl, [&] {
-    launch_root_with_pref(g, sa, acc, P->rs, P->pref, P->pref_stride, four, st);
+    launch_root_with_pref(g, sa, acc, P->rs, P->pref, P->pref_stride, st);
   });
   if (four) {
     run("vsum2", nl, [&] { launch_vsum2_four(g, sa, acc, st); });
@@ -757,8 +757,8 @@ int count_launches(const evoke_plan* P, bool with_out) {
   if (P->batch) k += 1 + sl;
   if (P->relabel) k += 6 + (P->rl_long_rows ? 1 : 0) + (P->n > P->rl_long_rows ? 1 : 0);
   const bool four = P->cfg.orbits == 15;
-  // degrees, rev, dag, tri_count, tri_scan, tri_fill, [tri_edge], vsum1, tri_opp1
-  k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + (four ? 0 : sl) + nl + nl;
+  // degrees, rev, dag, tri_count, tri_scan, tri_fill, tri_edge, vsum1, tri_opp1
+  k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + sl + nl + nl;
   // k4, schedule, root
   k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl;
   // [link, k5, tri_opp2], vsum2, [vsum3]

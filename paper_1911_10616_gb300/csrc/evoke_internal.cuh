@@ -222,9 +222,8 @@ struct RootScratch {
 u32 root_map_stride(u32 map_n);
 size_t root_scratch_bytes(u32 map_stride, int ctas);
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
-// four: the 4-vertex-orbit variant (wedges and C4(u) only)
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
-                           u32* pref, u32 pref_stride, bool four, cudaStream_t st);
+                           u32* pref, u32 pref_stride, cudaStream_t st);
 void root_configure();  // host-side set-up (kernel attributes)
 void link_configure();  // host-side set-up (kernel attributes)
 void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,

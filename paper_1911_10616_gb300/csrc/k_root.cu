@@ -131,9 +131,8 @@ __device__ __forceinline__ u64 seg_sum(u32 key, u64 val, bool* is_tail) {
   return val;
 }
 
-// kFour: only what the 4-vertex orbits need (W -> C4(u) = DM8)
-template <int kThreads, bool kFour>
-__global__ void __launch_bounds__(kThreads)
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads)
 root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* pref_all,
             u32 pref_stride) {
   constexpr u32 kCold = 0x40000000u;  // W bit 30: the cold record is in use
@@ -240,7 +239,7 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       tp = t;
     }
 
-    if constexpr (!kFour) {
+    {
     // phase 2a: diamonds.  Triangle (u,a,b) with a < b; every y in
     // N(a)^N(b) other than u closes a diamond with chord (a,b) and u, y off
     // the chord.  Each warp takes 32 triangle-list entries of u at a time and
@@ -446,21 +445,11 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
       tp = t;
     }
 
-    }  // !kFour
+    }
 
     // phase 3b: scan the map (orbits 8, 36, 50; the 5-cycle credits of the
     // path ends), reset it
-    if constexpr (kFour) {
-      u64 a8 = 0;
-      const u32 nt = s_nt;
-      for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
-        MapHot* hx = HP(touched[idx] - cb);
-        a8 += c2(hx->W & kW);
-        *hx = MapHot{};
-      }
-      a8 = block_sum(a8, s_red);
-      if (threadIdx.x == 0) acc[(u64)A_DM8 * n + u] = a8;
-    } else {
+    {
       u64 a8 = 0, a36 = 0, a50 = 0, a5 = 0;
       const u32 nt = s_nt;
       for (u32 idx = threadIdx.x; idx < nt; idx += blockDim.x) {
@@ -812,15 +801,15 @@ void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st)
 }
 
 namespace {
-// Shared memory left for map records when `per_sm` CTAs of root_kernel<T, F>
+// Shared memory left for map records when `per_sm` CTAs of root_kernel<T>
 // share an SM; sets the kernel's dynamic shared-memory limit once.
-template <int T, bool F>
+template <int T>
 size_t root_dyn_smem(int per_sm) {
   static size_t static_smem = 0, per_sm_smem = 0, reserved = 0, optin = 0;
   static bool ready = false;
   if (!ready) {
     cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, root_kernel<T, F>);
+    cudaFuncGetAttributes(&fa, root_kernel<T>);
     int dev = 0, a = 0, b = 0, c = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&a, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -831,7 +820,7 @@ size_t root_dyn_smem(int per_sm) {
     reserved = (size_t)b;
     optin = (size_t)c;
     const size_t cap = optin > static_smem ? optin - static_smem : 0;
-    cudaFuncSetAttribute(root_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+    cudaFuncSetAttribute(root_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
     ready = true;
   }
   if (per_sm < 1) per_sm = 1;
@@ -844,7 +833,7 @@ size_t root_dyn_smem(int per_sm) {
 }  // namespace
 
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
-                           u32* pref, u32 pref_stride, bool four, cudaStream_t st) {
+                           u32* pref, u32 pref_stride, cudaStream_t st) {
   if (!g.n) return;
   cudaMemsetAsync(rs.head, 0, sizeof(u32), st);
   int dev = 0, sms = 1;
@@ -853,10 +842,10 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
   const int per_sm = (rs.ctas + sms - 1) / sms;
   size_t dyn = 0;
   switch (rs.threads) {
-    case 64: dyn = four ? root_dyn_smem<64, true>(per_sm) : root_dyn_smem<64, false>(per_sm); break;
-    case 128: dyn = four ? root_dyn_smem<128, true>(per_sm) : root_dyn_smem<128, false>(per_sm); break;
-    case 256: dyn = four ? root_dyn_smem<256, true>(per_sm) : root_dyn_smem<256, false>(per_sm); break;
-    default: dyn = four ? root_dyn_smem<512, true>(per_sm) : root_dyn_smem<512, false>(per_sm);
+    case 64: dyn = root_dyn_smem<64>(per_sm); break;
+    case 128: dyn = root_dyn_smem<128>(per_sm); break;
+    case 256: dyn = root_dyn_smem<256>(per_sm); break;
+    default: dyn = root_dyn_smem<512>(per_sm);
   }
   u64 recs = dyn / sizeof(MapHot);
   // more records than this cost the root pass more L1 cache than they save
@@ -871,29 +860,19 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
   }
   rs.smem_recs = (u32)recs;
   dyn = (size_t)recs * sizeof(MapHot);
-#define EVOKE_ROOT_LAUNCH(T)                                                               \
-  do {                                                                                     \
-    if (four) root_kernel<T, true><<<rs.ctas, T, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); \
-    else root_kernel<T, false><<<rs.ctas, T, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);     \
-  } while (0)
   switch (rs.threads) {
-    case 64: EVOKE_ROOT_LAUNCH(64); break;
-    case 128: EVOKE_ROOT_LAUNCH(128); break;
-    case 256: EVOKE_ROOT_LAUNCH(256); break;
-    default: EVOKE_ROOT_LAUNCH(512);
+    case 64: root_kernel<64><<<rs.ctas, 64, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
+    case 128: root_kernel<128><<<rs.ctas, 128, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
+    case 256: root_kernel<256><<<rs.ctas, 256, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
+    default: root_kernel<512><<<rs.ctas, 512, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
   }
-#undef EVOKE_ROOT_LAUNCH
 }
 
 void root_configure() {
-  root_dyn_smem<64, false>(16);
-  root_dyn_smem<128, false>(8);
-  root_dyn_smem<256, false>(4);
-  root_dyn_smem<512, false>(2);
-  root_dyn_smem<64, true>(16);
-  root_dyn_smem<128, true>(8);
-  root_dyn_smem<256, true>(4);
-  root_dyn_smem<512, true>(2);
+  root_dyn_smem<64>(16);
+  root_dyn_smem<128>(8);
+  root_dyn_smem<256>(4);
+  root_dyn_smem<512>(2);
 }
 
 void link_configure() {
