@@ -252,6 +252,32 @@ def max_over_ranks(x, dist):
     return float(t.item())
 
 
+PROFILE_DRAM = {
+    # workload -> committed ncu summary holding the root kernel's DRAM bytes
+    "chung_lu_1m": "profiles/root_kernel_dram_chung_lu_1m.md",
+}
+
+
+def measured_traffic(workload):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one root_kernel launch
+    from the committed ncu summary, or None when there is none or the kernel
+    source changed since it was captured (the summary records its sha1)."""
+    import hashlib
+    import re
+    rel = PROFILE_DRAM.get(workload)
+    if rel is None or not os.path.exists(os.path.join(ROOT, rel)):
+        return None
+    text = open(os.path.join(ROOT, rel)).read()
+    t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    h = re.search(r"k_root_cu_sha1:\s*([0-9a-f]{40})", text)
+    if not t or not h:
+        return None
+    src = os.path.join(ROOT, "paper_1911_10616_gb300", "csrc", "k_root.cu")
+    if hashlib.sha1(open(src, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return int(t.group(1))
+
+
 def roofline_of(phases, g, ev, rp, col, n, m, args, four=False):
     peak, peak_kind = read_peaks()
     if not phases:
@@ -271,8 +297,9 @@ def roofline_of(phases, g, ev, rp, col, n, m, args, four=False):
     else:
         alg_bytes = 4 * (2 * m) + 8 * n  # lower bound: one read of the CSR
     achieved = alg_bytes / per_launch_s / 1e9
+    traffic = measured_traffic(args.workload) if name == "root" else None
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
             "algorithmic_bytes": alg_bytes, "launch_ms": per_launch_s * 1000.0, "units": ent}
 
 

@@ -143,6 +143,13 @@ int evoke_plan_launch_graph(evoke_plan* plan, int64_t* out, void* stream);
  * (when evoke_profile_enable is on); same kernels, same results. */
 int evoke_plan_execute_profiled(evoke_plan* plan, int64_t* out, void* stream);
 int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* stats);
+/* Device-side status of the plan's latest execution on `stream`: synchronises
+ * the stream, then returns EVOKE_EOVERFLOW if a 32-bit per-pair 3-path count
+ * of the 5-cycle pass wrapped (the counts of that execution are then not
+ * exact), EVOKE_ECUDA if the stream failed, else EVOKE_OK.  Executions are
+ * asynchronous, so this is how a caller of evoke_plan_execute or
+ * evoke_plan_launch_graph learns of an overflow. */
+int evoke_plan_status(const evoke_plan* plan, void* stream);
 /* Autotuning hook: threads per CTA (64, 128, 256 or 512; the narrow shapes
  * suit batches of small graphs) and the number of persistent CTAs of the
  * per-root pass, at most root_ctas_max of evoke_plan_info. */

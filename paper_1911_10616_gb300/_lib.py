@@ -30,6 +30,7 @@ SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
            "evoke_orbit_matrix",
            "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
            "evoke_plan_launch_graph", "evoke_plan_execute_profiled", "evoke_plan_info", "evoke_plan_set_tuning",
+           "evoke_plan_status",
            "evoke_plan_destroy", "evoke_plan_set_model", "evoke_plan_features",
            "evoke_plan_root_timing", "evoke_mlp_forward", "evoke_mlp_grad", "evoke_mlp_train",
            "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = True):
         lib.evoke_plan_launch_graph.argtypes = [vp, vp, vp]
         lib.evoke_plan_execute_profiled.argtypes = [vp, vp, vp]
         lib.evoke_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
+        lib.evoke_plan_status.argtypes = [vp, vp]
+        lib.evoke_plan_status.restype = ctypes.c_int
         lib.evoke_plan_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.evoke_plan_destroy.argtypes = [vp]
         lib.evoke_plan_set_model.argtypes = [vp, vp]
@@ -277,6 +280,11 @@ class Plan:
         _check(load().evoke_plan_launch_graph(self._h, _ptr(out), _stream_handle(stream)),
                "evoke_plan_launch_graph")
         return out
+
+    def status(self, stream=None):
+        """Raise EvokeError if the latest execution's device checks failed
+        (a wrapped 32-bit 3-path count: EVOKE_EOVERFLOW); synchronises."""
+        _check(load().evoke_plan_status(self._h, _stream_handle(stream)), "evoke_plan_status")
 
     def info(self) -> dict:
         st = PlanStats()

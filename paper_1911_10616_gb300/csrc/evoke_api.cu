@@ -990,6 +990,15 @@ int evoke_plan_execute(evoke_plan* plan, int64_t* out, void* stream) {
   return cudaGetLastError() == cudaSuccess ? EVOKE_OK : EVOKE_ECUDA;
 }
 
+int evoke_plan_status(const evoke_plan* plan, void* stream) {
+  if (!plan) return EVOKE_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int ovf = 0;
+  cudaMemcpyAsync(&ovf, plan->status + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return EVOKE_ECUDA;
+  return ovf ? EVOKE_EOVERFLOW : EVOKE_OK;
+}
+
 int evoke_plan_execute_profiled(evoke_plan* plan, int64_t* out, void* stream) {
   if (!plan || (plan->n && !out)) return EVOKE_EINVAL;
   execute(plan, reinterpret_cast<long long*>(out), static_cast<cudaStream_t>(stream),

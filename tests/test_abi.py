@@ -43,6 +43,7 @@ def test_null_arguments_rejected_without_gpu_work():
     lib = _lib.load()
     assert lib.evoke_orbit_matrix(None) == 1
     assert lib.evoke_count_orbits(None, None, 5, 3, None, None, None) == 1
+    assert lib.evoke_plan_status(None, None) == 1
 
 
 def test_totals_argument_checks_and_empty_input_without_gpu():
