@@ -332,6 +332,14 @@ def run_single(args, rank, world, dist, barrier):
         tune.append((timed(lambda: plan.execute(out), 1, stream, barrier), th, ct))
     best = min(tune)
     plan.set_tuning(best[1], best[2])
+    # autotune the root order: degree buckets, or grouped by highest-degree
+    # neighbour in chunks of 16
+    sched_t = []
+    for sched, chunk in ((0, 1), (1, 16)):
+        plan.set_schedule(sched, chunk)
+        sched_t.append((timed(lambda: plan.execute(out), 1, stream, barrier), sched, chunk))
+    best_sched = min(sched_t)
+    plan.set_schedule(best_sched[1], best_sched[2])
     for _ in range(args.warmup):
         plan.execute(out)
     barrier()
@@ -365,7 +373,7 @@ def run_single(args, rank, world, dist, barrier):
         def e2e_step():
             d_rp.copy_(h_rp, non_blocking=True)
             d_col.copy_(h_col, non_blocking=True)
-            ev.count_orbits(d_rp, d_col, n, m, out=out, orbits=orbits)
+            ev.count_orbits(d_rp, d_col, n, m, out=out, orbits=orbits, schedule=best_sched[1])
             h_out.copy_(out, non_blocking=True)
 
         e2e_t = max(max_over_ranks(timed(e2e_step, args.e2e_steps, stream, barrier), dist), 1e-12)
@@ -390,7 +398,11 @@ def run_single(args, rank, world, dist, barrier):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
         "config": {"workload": desc, "n": n, "m": m, "seed": seed,
-                   "parallelism": f"replicas{world}", "schedule": "degree-bucket",
+                   "parallelism": f"replicas{world}",
+                   "schedule": ("degree-bucket" if best_sched[1] == 0 else
+                                f"grouped by highest-degree neighbour, chunks of {best_sched[2]}"),
+                   "schedule_s": {("degree-bucket" if sc == 0 else f"hub-grouped/{ch}"): round(t, 4)
+                                  for t, sc, ch in sched_t},
                    "l2": "working set (CSR + per-edge arrays, GBs) far larger than the 129 MB L2",
                    "triangles": info["triangles"], "max_degree": info["max_degree"],
                    "tuned_root": {"threads": best[1], "ctas": best[2]},

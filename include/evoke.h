@@ -54,7 +54,10 @@ extern "C" {
 typedef struct evoke_opts {
   int32_t validate;   /* nonzero: check the CSR invariants first (syncs the stream) */
   int32_t root_ctas;  /* persistent CTAs of the per-root pass; 0 = 2 per SM */
-  int32_t schedule;   /* 0 = degree-bucket schedule (decreasing wedge work) */
+  int32_t schedule;   /* order of the per-root pass: 0 = degree-bucket schedule
+                         (decreasing wedge work); 1 = roots grouped by their
+                         highest-degree neighbour, taken by the CTAs in chunks
+                         of 8 consecutive roots (see evoke_plan_set_schedule) */
   int32_t orbits;     /* 0 or 73: all 73 orbits, out is int64[n*73];
                          15: the 4-vertex orbits 0..14 only (Thm. 4orbit,
                          Lem. 4vertexorbit), out is int64[n*15]; the passes
@@ -154,6 +157,10 @@ int evoke_plan_status(const evoke_plan* plan, void* stream);
  * suit batches of small graphs) and the number of persistent CTAs of the
  * per-root pass, at most root_ctas_max of evoke_plan_info. */
 int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_ctas);
+/* Root order of later executions: schedule 0 (degree-bucket) or 1 (grouped by
+ * highest-degree neighbour, `chunk` consecutive roots per queue grab, 1..4096).
+ * Counts do not depend on it.  Errors: EVOKE_EINVAL. */
+int evoke_plan_set_schedule(evoke_plan* plan, int32_t schedule, int32_t chunk);
 int evoke_plan_destroy(evoke_plan* plan);
 
 /*

@@ -30,7 +30,7 @@ SYMBOLS = ("evoke_count_orbits", "evoke_count_batch", "evoke_build_dag",
            "evoke_orbit_matrix",
            "evoke_plan_create", "evoke_plan_create_batch", "evoke_plan_execute",
            "evoke_plan_launch_graph", "evoke_plan_execute_profiled", "evoke_plan_info", "evoke_plan_set_tuning",
-           "evoke_plan_status",
+           "evoke_plan_status", "evoke_plan_set_schedule",
            "evoke_plan_destroy", "evoke_plan_set_model", "evoke_plan_features",
            "evoke_plan_root_timing", "evoke_mlp_forward", "evoke_mlp_grad", "evoke_mlp_train",
            "evoke_profile_enable", "evoke_profile_read", "evoke_profile_reset",
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True):
         lib.evoke_plan_execute_profiled.argtypes = [vp, vp, vp]
         lib.evoke_plan_info.argtypes = [vp, ctypes.POINTER(PlanStats)]
         lib.evoke_plan_status.argtypes = [vp, vp]
+        lib.evoke_plan_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        lib.evoke_plan_set_schedule.restype = ctypes.c_int
         lib.evoke_plan_status.restype = ctypes.c_int
         lib.evoke_plan_set_tuning.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         lib.evoke_plan_destroy.argtypes = [vp]
@@ -179,7 +181,8 @@ def _orbits(orbits: int) -> int:
 
 
 def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = False,
-                 root_ctas: int = 0, stream=None, orbits: int = 73, induced: bool = True):
+                 root_ctas: int = 0, stream=None, orbits: int = 73, induced: bool = True,
+                 schedule: int = 0):
     """Orbit counts, int64 tensor [n, orbits] on the graph's device (orbits =
     73: all; 15: the 4-vertex orbits 0..14 only); induced=False gives the
     non-induced counts DM."""
@@ -190,7 +193,7 @@ def count_orbits(rowptr, colidx, n: int, m: int, out=None, validate: bool = Fals
         out = torch.empty((n, k), dtype=torch.int64, device=rowptr.device)
     elif out.dtype != torch.int64 or out.numel() != n * k or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous int64 tensor with n*{k} entries")
-    opts = EvokeOpts(1 if validate else 0, int(root_ctas), 0, k, 0 if induced else 1)
+    opts = EvokeOpts(1 if validate else 0, int(root_ctas), int(schedule), k, 0 if induced else 1)
     rc = load().evoke_count_orbits(_ptr(rowptr), _ptr(colidx), n, m, _ptr(out),
                                    ctypes.byref(opts), _stream_handle(stream))
     _check(rc, "evoke_count_orbits")
@@ -294,6 +297,12 @@ class Plan:
     def set_tuning(self, root_threads: int, root_ctas: int):
         _check(load().evoke_plan_set_tuning(self._h, int(root_threads), int(root_ctas)),
                "evoke_plan_set_tuning")
+
+    def set_schedule(self, schedule: int, chunk: int = 8):
+        """Root order: 0 degree-bucket, 1 grouped by highest-degree neighbour
+        with `chunk` roots per queue grab."""
+        _check(load().evoke_plan_set_schedule(self._h, int(schedule), int(chunk)),
+               "evoke_plan_set_schedule")
 
     def set_model(self, params):
         """Attach MLP parameters (float32 CUDA tensor of 1249) or None."""

@@ -357,6 +357,8 @@ struct Config {
   u32 link_warps = 0;     // 0: 64 per SM
   int orbits = 73;        // 73, or 15: the 4-vertex orbits only
   bool induced = true;    // false: write the non-induced counts DM
+  int schedule = 0;       // 0: degree-bucket; 1: grouped by highest-degree neighbour
+  u32 chunk = 8;          // roots per queue grab under schedule 1
 };
 
 // evoke_opts.orbits: 0 or 73 -> all orbits, 15 -> orbits 0..14; else -1
@@ -661,6 +663,7 @@ int plan_stage2(evoke_plan* P) {
   rs.bucket_cnt = ar.take<u32>(256);
   rs.head = ar.take<u32>(4);
   rs.tsrc = P->acc + (size_t)A_TSRC * n;
+  rs.chunk = 1;
   rs.cta_end = nullptr;
   rs.prof = root_profile ? ar.take<u64>(8) : nullptr;
   rs.cycles = nullptr;
@@ -724,9 +727,13 @@ void execute(evoke_plan* P, long long* out, cudaStream_t st, bool timed) {
       launch_features(g, acc, P->feat, st);
       launch_mlp_forward(P->feat, n, P->model, P->prio, st);
     });
+    P->rs.chunk = 1;
     run("schedule", 3 * nl, [&] {
       launch_priority_schedule(P->prio, n, P->rs.bucket_cnt, P->rs.head, P->rs.order, st);
     });
+  } else if (P->cfg.schedule == 1) {
+    P->rs.chunk = P->cfg.chunk;
+    run("schedule", n ? 5 : 0, [&] { launch_hub_schedule(g, P->rs, P->cnt, P->scan_tmp, st); });
   } else {
     run("schedule", 3 * nl, [&] { launch_schedule(g, acc, P->rs, st); });
   }
@@ -760,7 +767,8 @@ int count_launches(const evoke_plan* P, bool with_out) {
   // degrees, rev, dag, tri_count, tri_scan, tri_fill, tri_edge, vsum1, tri_opp1
   k += nl + nl + (P->n ? 5 : 0) + sl + (P->g.S ? 3 : 0) + sl + sl + nl + nl;
   // k4, schedule, root
-  k += (P->ntri_entries ? 1 : 0) + sl + 3 * nl + nl;
+  const int sched = (!P->model && P->cfg.schedule == 1) ? (P->n ? 5 : 0) : 3 * nl;
+  k += (P->ntri_entries ? 1 : 0) + sl + sched + nl;
   // [link, k5, tri_opp2], vsum2, [vsum3]
   k += four ? nl : sl + (P->k5.blocks ? 1 : 0) + nl + nl + nl;
   if (P->model) k += 2 * nl;
@@ -804,6 +812,7 @@ int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, ui
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
   P->cfg.orbits = opts_orbits(opts);
   P->cfg.induced = !(opts && opts->noninduced);
+  if (opts && opts->schedule == 1) P->cfg.schedule = 1;
   if (P->cfg.orbits < 0) {
     plan_free(P);
     return EVOKE_EINVAL;
@@ -947,6 +956,7 @@ int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_c
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
   P->cfg.orbits = opts_orbits(opts);
   P->cfg.induced = !(opts && opts->noninduced);
+  if (opts && opts->schedule == 1) P->cfg.schedule = 1;
   if (P->cfg.orbits < 0) {
     delete P;
     return EVOKE_EINVAL;
@@ -1073,6 +1083,18 @@ int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_c
   plan->cfg.root_threads = root_threads;
   plan->rs.threads = root_threads;
   plan->rs.ctas = root_ctas;
+  return EVOKE_OK;
+}
+
+int evoke_plan_set_schedule(evoke_plan* plan, int32_t schedule, int32_t chunk) {
+  if (!plan || (schedule != 0 && schedule != 1) || chunk < 1 || chunk > 4096) return EVOKE_EINVAL;
+  if (plan->gexec) {
+    cudaGraphExecDestroy(plan->gexec);
+    plan->gexec = nullptr;
+  }
+  plan->cfg.schedule = schedule;
+  plan->cfg.chunk = (u32)chunk;
+  plan->launches_per_exec = count_launches(plan, true);
   return EVOKE_OK;
 }
 

@@ -214,6 +214,7 @@ struct RootScratch {
   u64* cycles;   // optional [n]: cycles per root
   u64* cta_end;  // optional [ctas]: global timer (ns) when each CTA ran out of roots
   int ctas;
+  u32 chunk;     // roots a CTA takes from the queue at a time (1: one by one)
   u32 smem_recs; // hot records of ids [0, smem_recs) kept in shared memory (set at launch)
 };
 // per-CTA record stride: at least map_n, an odd number of 128-byte lines of
@@ -222,6 +223,9 @@ struct RootScratch {
 u32 root_map_stride(u32 map_n);
 size_t root_scratch_bytes(u32 map_stride, int ctas);
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st);
+// roots grouped by their highest-degree neighbour (cnt: scratch of n entries)
+void launch_hub_schedule(const Graph& g, RootScratch& rs, u32* cnt, void* scan_tmp,
+                         cudaStream_t st);
 void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootScratch& rs,
                            u32* pref, u32 pref_stride, cudaStream_t st);
 void root_configure();  // host-side set-up (kernel attributes)

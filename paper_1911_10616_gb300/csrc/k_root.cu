@@ -24,6 +24,11 @@ namespace {
 constexpr u32 kFlag = 0x80000000u;
 constexpr u32 kCnt = 0x7fffffffu;
 
+// bring the line holding *p into L2 without waiting for it
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // largest i in [0, len) with pref[i] <= w   (pref ascending, pref[0] = 0)
 __device__ __forceinline__ u32 seg_find(const u32* pref, u32 len, u32 w) {
   u32 lo = 0, hi = len;
@@ -159,15 +164,21 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
   __shared__ u32 s_pref[kSmemPref + 1];
   __shared__ u32 s_nrp[kSmemPref];            // rowptr of each neighbour (small roots)
   __shared__ unsigned char s_nout[kSmemPref];  // u -> neighbour in the DAG
-  __shared__ u32 s_root, s_nt, s_nj, s_carry;
+  __shared__ u32 s_root, s_nt, s_nj, s_carry, s_next, s_end;
   __shared__ u64 s_red[32];
   __shared__ long long s_t0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   u32* gpref = pref_all + (u64)blockIdx.x * pref_stride;
 
+  if (threadIdx.x == 0) s_next = s_end = 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      s_root = atomicAdd(rs.head, 1u);
+      // roots come from the queue in chunks of rs.chunk consecutive entries
+      if (s_next >= s_end) {
+        s_next = atomicAdd(rs.head, rs.chunk);
+        s_end = min(s_next + rs.chunk, n);
+      }
+      s_root = s_next < s_end ? s_next++ : n;
       s_nt = 0;
       s_nj = 0;
       s_t0 = clock64();
@@ -220,17 +231,35 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     };
 
     // phase 1: wedges u - v - x.  W (low word) and Wn (high word) of the hot
-    // record are bumped by one 64-bit atomic.
-    for (u32 w = threadIdx.x; w < total; w += blockDim.x) {
-      u32 i, t;
-      bool out;
-      wedge(w, i, t, out);
-      const u32 x = g.col[t];
-      if (x == u) continue;
-      const bool in_in = out && g.sin[t];  // u -> v <- x
-      const u64 old = atomicAdd(reinterpret_cast<u64*>(&HP(x - cb)->W),
-                                in_in ? 1ull : (1ull | (1ull << 32)));
-      if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
+    // record are bumped by one 64-bit atomic.  An atomic that misses L2 is far
+    // slower to serve than a read miss, so each thread prefetches the record
+    // of its next wedge into L2 before it performs the current atomic.
+    {
+      constexpr u32 kNone = 0xffffffffu;
+      auto target = [&](u32 w, u32& x, bool& in_in) {
+        u32 i, t;
+        bool out;
+        wedge(w, i, t, out);
+        x = g.col[t];
+        in_in = out && g.sin[t];  // u -> v <- x
+        if (x == u) x = kNone;
+        else if (x - cb >= K) prefetch_l2(H + (x - cb));
+      };
+      u32 x = kNone;
+      bool in_in = false;
+      if (threadIdx.x < total) target(threadIdx.x, x, in_in);
+      for (u32 w = threadIdx.x; w < total; w += blockDim.x) {
+        u32 xn = kNone;
+        bool inn = false;
+        if (w + blockDim.x < total) target(w + blockDim.x, xn, inn);
+        if (x != kNone) {
+          const u64 old = atomicAdd(reinterpret_cast<u64*>(&HP(x - cb)->W),
+                                    in_in ? 1ull : (1ull | (1ull << 32)));
+          if ((u32)old == 0) touched[atomicAdd(&s_nt, 1u)] = x;
+        }
+        x = xn;
+        in_in = inn;
+      }
     }
     __syncthreads();
     if (rs.prof && threadIdx.x == 0) {
@@ -320,8 +349,12 @@ root_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc, RootScratch rs, u32* 
     for (u32 idx = wid; idx < du; idx += nw) {
       const u32 k = g.col[ub + idx];
       if (!prec(g.deg, k, u)) continue;  // k -> u
-      for (u32 p = g.dag_ptr[k] + lane; p < g.dag_ptr[k + 1]; p += 32) {
+      const u32 pe = g.dag_ptr[k + 1];
+      // the cold records are first touched here: prefetch each lane's next one
+      if (g.dag_ptr[k] + lane < pe) prefetch_l2(C + (g.dag_col[g.dag_ptr[k] + lane] - cb));
+      for (u32 p = g.dag_ptr[k] + lane; p < pe; p += 32) {
         const u32 x = g.dag_col[p];
+        if (p + 32 < pe) prefetch_l2(C + (g.dag_col[p + 32] - cb));
         if (x == u) continue;
         const u32 sk = g.dag_slot[p];
         const u64 old = atomicAdd(&C[x - cb].RY, (1ull << 32) | (u64)sa.Mtop[sk]);
@@ -789,6 +822,33 @@ u32 root_map_stride(u32 map_n) {
 size_t root_scratch_bytes(u32 map_stride, int ctas) {
   return (size_t)ctas * map_stride * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32)) +
          16 * 256;
+}
+
+// --- hub-grouped schedule: roots ordered by their highest-degree neighbour --
+// After the relabelling by decreasing degree that neighbour is the first entry
+// of the row.  Roots that share it have largely the same 2-hop set, so a CTA
+// that takes several of them in a row re-touches the same map lines (and the
+// same adjacency row) while they are still cached.  Counting sort by that key.
+__device__ __forceinline__ u32 hub_key(const Graph& g, u32 u) {
+  const u32 b = g.rowptr[u];
+  return g.rowptr[u + 1] > b ? g.col[b] : g.n - 1;
+}
+__global__ void hub_hist_kernel(Graph g, u32* cnt) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < g.n) atomicAdd(&cnt[hub_key(g, u)], 1u);
+}
+__global__ void hub_scatter_kernel(Graph g, u32* cursor, u32* order) {
+  const u32 u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < g.n) order[atomicAdd(&cursor[hub_key(g, u)], 1u)] = u;
+}
+
+void launch_hub_schedule(const Graph& g, RootScratch& rs, u32* cnt, void* scan_tmp,
+                         cudaStream_t st) {
+  if (!g.n) return;
+  cudaMemsetAsync(cnt, 0, sizeof(u32) * g.n, st);
+  hub_hist_kernel<<<(g.n + 255) / 256, 256, 0, st>>>(g, cnt);
+  launch_scan_u32_inplace(cnt, g.n, scan_tmp, st);
+  hub_scatter_kernel<<<(g.n + 255) / 256, 256, 0, st>>>(g, cnt, rs.order);
 }
 
 void launch_schedule(const Graph& g, u64* acc, RootScratch& rs, cudaStream_t st) {

@@ -124,3 +124,25 @@ def test_build_dag(ev):
         want.setdefault(int(s), []).append(int(t))
     for u in range(g.n):
         assert sorted(want.get(u, [])) == dc[dp[u]:dp[u + 1]].tolist()
+
+
+def test_hub_grouped_schedule(ev, oracle_mod):
+    # the root order (degree buckets, or grouped by highest-degree neighbour
+    # in chunks) must not change any count
+    import torch
+    g = gg.chung_lu(20000, 100000, 2.1, 500, 3)
+    _, want = oracle_mod.formulas(g)
+    rp, col = ev.to_device(g)
+    plan = ev.Plan.single(rp, col, g.n, g.m)
+    out = plan.new_output()
+    for sched, chunk in ((1, 1), (1, 8), (1, 64), (0, 8)):
+        plan.set_schedule(sched, chunk)
+        out.fill_(-1)
+        plan.execute(out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want), (sched, chunk)
+    out.fill_(-1)
+    plan.set_schedule(1, 16)
+    plan.launch_graph(out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
