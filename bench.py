@@ -325,7 +325,7 @@ def run_single(args, rank, world, dist, barrier):
     sms = torch.cuda.get_device_properties(local_device()).multi_processor_count
     info0 = plan.info()
     tune = []
-    for th, ct in ((512, 2 * sms), (256, 4 * sms)):
+    for th, ct in ((512, 2 * sms), (1024, sms), (256, 4 * sms)):
         if ct > info0["root_ctas_max"]:
             continue
         plan.set_tuning(th, ct)

@@ -454,7 +454,7 @@ int check_csr(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64
 void apply_config(evoke_plan* P, u32 map_n) {
   const int sms = sm_count_cached();
   const int t = P->cfg.root_threads;
-  P->rs.threads = (t == 64 || t == 128 || t == 256) ? t : 512;
+  P->rs.threads = (t == 64 || t == 128 || t == 256 || t == 1024) ? t : 512;
   P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (1024 / P->rs.threads);
   // maps for up to 16 (small maps) or 4 CTAs per SM when that is cheap, so
   // that tuning can raise the CTA count later
@@ -1070,7 +1070,8 @@ int evoke_plan_info(const evoke_plan* plan, evoke_plan_stats* out) {
 
 int evoke_plan_set_tuning(evoke_plan* plan, int32_t root_threads, int32_t root_ctas) {
   if (!plan || root_ctas <= 0 ||
-      (root_threads != 64 && root_threads != 128 && root_threads != 256 && root_threads != 512))
+      (root_threads != 64 && root_threads != 128 && root_threads != 256 && root_threads != 512 &&
+       root_threads != 1024))
     return EVOKE_EINVAL;
   const int per_sm_max = 2048 / root_threads;
   if (root_ctas > sm_count_cached() * per_sm_max * 4) return EVOKE_ERANGE;

@@ -554,17 +554,23 @@ __global__ void sched_scatter_kernel(const u64* __restrict__ work, u32 n, u32* c
   if (u < n) order[atomicAdd(&cursor[63u - bucket_of(work[u])], 1u)] = u;
 }
 
-// --- wheel pass: 4-cycles through a inside N(u), for every slot (u,a) ------
-// (orbits 68 and 69: a wheel is a hub plus a 4-cycle in the hub's
-// neighbourhood).  W_ac = number of 2-paths a - b - c inside N(u), and the
-// 4-cycles through a are sum_{c != a} C(W_ac, 2).  W is symmetric, so the
-// pass for a counts only partners c > a (slot order = id order; each chord
-// list is entered by binary search), keeps sum_{c > a} C(W_ac, 2) and credits
-// C(W_ac, 2) to c once per pair.  One warp per slot (u,a); the warp walks the
-// concatenated list tails of the b's 32 at a time.  Counters are 16-bit
-// halves of shared-memory words when d(u) <= kLinkSmem (then W < 2^16), else
-// 32-bit words of the warp's global scratch row; touched partners are listed
-// so that the counters can be credited and cleared.
+// --- wheel pass: 4-cycles inside N(u) per vertex, for every slot (u,a) -------
+// (orbits 68 and 69: a wheel is a hub u plus a 4-cycle of the link graph
+// G[N(u)], whose edges are the triangle-list entries of u's slots).  Each
+// 4-cycle of G[N(u)] is found once, from its top vertex a, the smallest id
+// (the highest degree after the relabelling): the wedges a - b - c with b > a
+// and c > a give W'(a,c) = |{b > a : b ~ a, b ~ c}|, and C(W'(a,c), 2) cycles
+// have top a and opposite vertex c.  They are credited to a and to c, and the
+// middle b of each wedge a - b - c gets W'(a,c) - 1 (one per other middle), so
+// every slot (u,x) ends with the number of 4-cycles of G[N(u)] through x.
+// Ordering the tops by degree is what keeps the wedge count down: a wedge
+// through a hub b is walked only from the few tops of still higher degree.
+// One warp per slot (u,a): it walks the b > a entries of tl(u,a) 32 at a time
+// and, for each, the tail c > a of tl(u,b) (entered by binary search; slot
+// order = id order).  Sweep 1 counts W' in 16-bit halves of shared-memory
+// words when d(u) <= kLinkSmem (then W' < 2^16), else in 32-bit words of the
+// warp's global scratch row, and lists the touched partners; sweep 2 walks
+// the same wedges again to credit the middles.
 constexpr int kLinkWarps = 8;
 constexpr u32 kLinkSmem = 2048;
 
@@ -578,6 +584,7 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
       reinterpret_cast<u32 (*)[kLinkSmem]>(link_smem + (size_t)kLinkWarps * (kLinkSmem / 2));
   __shared__ u32 s_pref[kLinkWarps][33];
   __shared__ u64 s_start[kLinkWarps][32];
+  __shared__ u32 s_sb[kLinkWarps][32];
   __shared__ u32 s_cnt[kLinkWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const u32 gw = blockIdx.x * kLinkWarps + wid;
@@ -588,19 +595,31 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
   __syncwarp();
   for (u64 s = gw; s < g.S; s += nwarps) {
     if (sa.T[s] < 2) continue;
+    const u64 q1 = g.tl_ptr[s + 1];
+    u64 kb = g.tl_ptr[s];
+    {  // first entry of tl(u,a) with b > a
+      u64 hi = q1;
+      while (kb < hi) {
+        const u64 mid = kb + ((hi - kb) >> 1);
+        if (g.tl[mid] <= (u32)s) kb = mid + 1;
+        else hi = mid;
+      }
+    }
+    if (q1 - kb < 2) continue;  // a cycle with top a needs two middles
     const u32 lo = g.col[g.rev[s]];  // the row owning slot s
     const u32 ub = g.rowptr[lo], du = g.rowptr[lo + 1] - ub;
     const bool small = du <= kLinkSmem;
     u32* list = small ? s_list[wid] : glist;
     if (lane == 0) s_cnt[wid] = 0;
     __syncwarp();
-    u64 c4 = 0;
-    for (u64 k0 = g.tl_ptr[s]; k0 < g.tl_ptr[s + 1]; k0 += 32) {
+    // the wedges of 32 b's at a time: per lane one b (slot sb, tail start
+    // and length), then the concatenated tails one entry per lane
+    auto load_chunk = [&](u64 k0) -> u32 {
       const u64 k = k0 + lane;
-      u32 len = 0;
+      u32 len = 0, sb = 0;
       u64 st0 = 0;
-      if (k < g.tl_ptr[s + 1]) {
-        const u32 sb = g.tl[k];
+      if (k < q1) {
+        sb = g.tl[k];
         u64 l2 = g.tl_ptr[sb], h2 = g.tl_ptr[sb + 1];
         const u64 end = h2;
         while (l2 < h2) {  // first partner slot > s
@@ -620,19 +639,28 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
       s_pref[wid][lane + 1] = incl;
       if (lane == 0) s_pref[wid][0] = 0;
       s_start[wid][lane] = st0;
+      s_sb[wid][lane] = sb;
       __syncwarp();
-      const u32 tot = s_pref[wid][32];
-      u32 l2 = 0;  // list of entry `it`; non-decreasing as `it` grows
-      for (u32 it = lane; it < tot; it += 32) {
-        if (s_pref[wid][l2 + 1] <= it) {
-          u32 h2 = 32;
-          ++l2;
-          while (h2 - l2 > 1) {
-            const u32 mid = (l2 + h2) >> 1;
-            if (s_pref[wid][mid] <= it) l2 = mid;
-            else h2 = mid;
-          }
+      return s_pref[wid][32];
+    };
+    auto next_list = [&](u32 it, u32& l2) {  // l2: list of entry it (non-decreasing)
+      if (s_pref[wid][l2 + 1] <= it) {
+        u32 h2 = 32;
+        ++l2;
+        while (h2 - l2 > 1) {
+          const u32 mid = (l2 + h2) >> 1;
+          if (s_pref[wid][mid] <= it) l2 = mid;
+          else h2 = mid;
         }
+      }
+    };
+    // sweep 1: W' per partner c, and the cycles with top a
+    u64 c4 = 0;
+    for (u64 k0 = kb; k0 < q1; k0 += 32) {
+      const u32 tot = load_chunk(k0);
+      u32 l2 = 0;
+      for (u32 it = lane; it < tot; it += 32) {
+        next_list(it, l2);
         const u32 pc = g.tl[s_start[wid][l2] + (it - s_pref[wid][l2])] - ub;
         u32 old;
         if (small) {
@@ -646,7 +674,7 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
       }
       __syncwarp();
     }
-    // credit each partner c > a with C(W_ac, 2) and clear its counter
+    // opposite vertices: C(W'(a,c), 2) each
     const u32 cnt = s_cnt[wid];
     for (u32 i = lane; i < cnt; i += 32) {
       const u32 pc = list[i];
@@ -658,6 +686,33 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
         w = gmap[pc];
       }
       if (w >= 2) atomicAdd(&sa.b68[ub + pc], (u64)w * (w - 1) / 2);
+    }
+    // sweep 2: each middle b of a wedge a - b - c gets W'(a,c) - 1
+    for (u64 k0 = kb; k0 < q1; k0 += 32) {
+      const u32 tot = load_chunk(k0);
+      const u32 iters = (tot + 31) & ~31u;
+      u32 l2 = 0;
+      for (u32 it = lane; it < iters; it += 32) {
+        u32 key = 0xffffffffu;
+        u64 add = 0;
+        if (it < tot) {
+          next_list(it, l2);
+          const u32 pc = g.tl[s_start[wid][l2] + (it - s_pref[wid][l2])] - ub;
+          u32 w;
+          if (small) {
+            const u32 sh = (pc & 1u) * 16u;
+            w = (s_map[wid][pc >> 1] >> sh) & 0xffffu;
+          } else {
+            w = gmap[pc];
+          }
+          key = l2;
+          add = w - 1;
+        }
+        bool tail;
+        const u64 sum = seg_sum(key, add, &tail);
+        if (tail && key != 0xffffffffu && sum) atomicAdd(&sa.b68[s_sb[wid][key]], sum);
+      }
+      __syncwarp();
     }
     __syncwarp();
     for (u32 i = lane; i < cnt; i += 32) {
@@ -905,25 +960,27 @@ void launch_root_with_pref(const Graph& g, const SlotArrays& sa, u64* acc, RootS
     case 64: dyn = root_dyn_smem<64>(per_sm); break;
     case 128: dyn = root_dyn_smem<128>(per_sm); break;
     case 256: dyn = root_dyn_smem<256>(per_sm); break;
+    case 1024: dyn = root_dyn_smem<1024>(per_sm); break;
     default: dyn = root_dyn_smem<512>(per_sm);
   }
-  u64 recs = dyn / sizeof(MapHot);
+  const u64 max_recs = dyn / sizeof(MapHot);
   // more records than this cost the root pass more L1 cache than they save
   // in map traffic (measured on the 1M-vertex Chung-Lu graph: 3,072 records
-  // per 512-thread CTA, 512 per 256-thread CTA)
-  const u64 cap = rs.threads == 512 ? 3072 : rs.threads == 256 ? 512 : recs;
-  if (recs > cap) recs = cap;
-  if (recs > rs.map_n) recs = rs.map_n;
-  if (const char* e = getenv("EVOKE_ROOT_SMEM_RECS")) {
+  // per 512- or 1024-thread CTA, 512 per 256-thread CTA)
+  const u64 cap = rs.threads >= 512 ? 3072 : rs.threads == 256 ? 512 : max_recs;
+  u64 recs = max_recs < cap ? max_recs : cap;
+  if (const char* e = getenv("EVOKE_ROOT_SMEM_RECS")) {  // tuning override
     const long long r = atoll(e);
-    if (r >= 0 && (u64)r < recs) recs = (u64)r;
+    if (r >= 0) recs = (u64)r < max_recs ? (u64)r : max_recs;
   }
+  if (recs > rs.map_n) recs = rs.map_n;
   rs.smem_recs = (u32)recs;
   dyn = (size_t)recs * sizeof(MapHot);
   switch (rs.threads) {
     case 64: root_kernel<64><<<rs.ctas, 64, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
     case 128: root_kernel<128><<<rs.ctas, 128, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
     case 256: root_kernel<256><<<rs.ctas, 256, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
+    case 1024: root_kernel<1024><<<rs.ctas, 1024, dyn, st>>>(g, sa, acc, rs, pref, pref_stride); break;
     default: root_kernel<512><<<rs.ctas, 512, dyn, st>>>(g, sa, acc, rs, pref, pref_stride);
   }
 }
@@ -933,6 +990,7 @@ void root_configure() {
   root_dyn_smem<128>(8);
   root_dyn_smem<256>(4);
   root_dyn_smem<512>(2);
+  root_dyn_smem<1024>(1);
 }
 
 void link_configure() {
