@@ -321,23 +321,31 @@ def run_single(args, rank, world, dist, barrier):
     plan = ev.Plan.single(rp, col, n, m, validate=True, orbits=orbits)
     out = plan.new_output()
     plan.execute(out)
-    # autotune the per-root pass shape (threads per CTA x persistent CTAs)
+    # autotune the per-root pass shape (threads per CTA x persistent CTAs),
+    # unless --root-shape fixes it
     sms = torch.cuda.get_device_properties(local_device()).multi_processor_count
     info0 = plan.info()
+    shapes = ((512, 2 * sms), (1024, sms), (256, 4 * sms))
+    if args.root_shape:
+        th, ct = (int(x) for x in args.root_shape.split("x"))
+        shapes = ((th, ct),)
     tune = []
-    for th, ct in ((512, 2 * sms), (1024, sms), (256, 4 * sms)):
+    for th, ct in shapes:
         if ct > info0["root_ctas_max"]:
             continue
         plan.set_tuning(th, ct)
-        tune.append((timed(lambda: plan.execute(out), 1, stream, barrier), th, ct))
+        tune.append((timed(lambda: plan.execute(out), 1, stream, barrier) if len(shapes) > 1 else 0.0,
+                     th, ct))
     best = min(tune)
     plan.set_tuning(best[1], best[2])
-    # autotune the root order: degree buckets, or grouped by highest-degree
-    # neighbour in chunks of 16
+    # autotune the root order (degree buckets, or grouped by highest-degree
+    # neighbour in chunks of 16), unless --schedule fixes it
+    orders = {"degree": ((0, 1),), "hub": ((1, 16),)}.get(args.schedule, ((0, 1), (1, 16)))
     sched_t = []
-    for sched, chunk in ((0, 1), (1, 16)):
+    for sched, chunk in orders:
         plan.set_schedule(sched, chunk)
-        sched_t.append((timed(lambda: plan.execute(out), 1, stream, barrier), sched, chunk))
+        sched_t.append((timed(lambda: plan.execute(out), 1, stream, barrier) if len(orders) > 1 else 0.0,
+                        sched, chunk))
     best_sched = min(sched_t)
     plan.set_schedule(best_sched[1], best_sched[2])
     for _ in range(args.warmup):
@@ -616,6 +624,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--per-graph-sample", type=int, default=500)
+    ap.add_argument("--root-shape", default="",
+                    help="fix the per-root pass shape, THREADSxCTAS (default: autotune)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "degree", "hub"],
+                    help="fix the root order (default: autotune)")
     ap.add_argument("--no-roofline", action="store_true",
                     help="skip the extra pass that sizes the roofline's algorithmic bytes")
     args = ap.parse_args()

@@ -352,7 +352,8 @@ __global__ void copy_i64_kernel(const u64* in, long long* out, u64 count) {
 // into a CUDA graph and replayed).
 // ---------------------------------------------------------------------------
 struct Config {
-  int root_threads = 512;
+  int root_threads = 0;   // 0: 512 for single graphs, 64 for batches of small graphs
+  bool tunable = true;    // false: one-shot call, no later set_tuning
   int root_ctas = 0;      // 0: 2 per SM (512 threads) / 4 per SM (256)
   u32 link_warps = 0;     // 0: 64 per SM
   int orbits = 73;        // 73, or 15: the 4-vertex orbits only
@@ -453,7 +454,7 @@ int check_csr(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64
 
 void apply_config(evoke_plan* P, u32 map_n) {
   const int sms = sm_count_cached();
-  const int t = P->cfg.root_threads;
+  const int t = P->cfg.root_threads ? P->cfg.root_threads : (P->batch ? 64 : 512);
   P->rs.threads = (t == 64 || t == 128 || t == 256 || t == 1024) ? t : 512;
   P->rs.ctas = P->cfg.root_ctas > 0 ? P->cfg.root_ctas : sms * (1024 / P->rs.threads);
   // maps for up to 16 (small maps) or 4 CTAs per SM when that is cheap, so
@@ -461,6 +462,7 @@ void apply_config(evoke_plan* P, u32 map_n) {
   const size_t per_cta =
       (size_t)root_map_stride(map_n) * (sizeof(MapHot) + sizeof(MapCold) + 2 * sizeof(u32));
   P->ctas_alloc = P->rs.ctas;
+  if (!P->cfg.tunable) return;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)4 << 30;
   const size_t budget = std::min<size_t>(free_b / 3, (size_t)64 << 30);
@@ -798,7 +800,8 @@ int plan_finish_create(evoke_plan* P, evoke_plan** out_plan) {
 }
 
 int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uint64_t m,
-                  const evoke_opts* opts, cudaStream_t st, evoke_plan** out_plan) {
+                  const evoke_opts* opts, cudaStream_t st, evoke_plan** out_plan,
+                  bool tunable = true) {
   int rc = ensure_transform();
   if (rc) return rc;
   rc = check_csr(rowptr, colidx, n, m, st);
@@ -809,6 +812,7 @@ int create_single(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, ui
   P->n = n;
   P->m = m;
   P->st = st;
+  P->cfg.tunable = tunable;
   if (opts && opts->root_ctas > 0) P->cfg.root_ctas = opts->root_ctas;
   P->cfg.orbits = opts_orbits(opts);
   P->cfg.induced = !(opts && opts->noninduced);
@@ -1222,7 +1226,7 @@ int evoke_count_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t 
   if (n && !out) return EVOKE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   evoke_plan* P = nullptr;
-  int rc = create_single(rowptr, colidx, n, m, opts, st, &P);
+  int rc = create_single(rowptr, colidx, n, m, opts, st, &P, /*tunable=*/false);
   if (rc) return rc;
   rc = run_once(P, reinterpret_cast<long long*>(out), st);
   plan_free(P);
@@ -1251,7 +1255,7 @@ int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n
   if (!tri && !c4 && !k4 && !e7 && !e9) return EVOKE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   evoke_plan* P = nullptr;
-  int rc = create_single(rowptr, colidx, n, m, nullptr, st, &P);
+  int rc = create_single(rowptr, colidx, n, m, nullptr, st, &P, /*tunable=*/false);
   if (rc) return rc;
   rc = run_once(P, nullptr, st);
   const u64 S = P->g.S;
@@ -1296,7 +1300,7 @@ int evoke_edge_orbit_counts(const uint32_t* rowptr, const uint32_t* colidx, uint
   if (!out && m) return EVOKE_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   evoke_plan* P = nullptr;
-  int rc = create_single(rowptr, colidx, n, m, nullptr, st, &P);
+  int rc = create_single(rowptr, colidx, n, m, nullptr, st, &P, /*tunable=*/false);
   if (rc) return rc;
   rc = run_once(P, nullptr, st);
   const u64 S = P->g.S;

@@ -656,8 +656,10 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
     };
     // sweep 1: W' per partner c, and the cycles with top a
     u64 c4 = 0;
+    u32 tot1 = 0;  // entries of the (last) chunk
     for (u64 k0 = kb; k0 < q1; k0 += 32) {
       const u32 tot = load_chunk(k0);
+      tot1 = tot;
       u32 l2 = 0;
       for (u32 it = lane; it < tot; it += 32) {
         next_list(it, l2);
@@ -687,9 +689,11 @@ link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
       }
       if (w >= 2) atomicAdd(&sa.b68[ub + pc], (u64)w * (w - 1) / 2);
     }
-    // sweep 2: each middle b of a wedge a - b - c gets W'(a,c) - 1
+    // sweep 2: each middle b of a wedge a - b - c gets W'(a,c) - 1.  With one
+    // chunk only, its tables are still in shared memory from sweep 1.
+    const bool one_chunk = q1 - kb <= 32;
     for (u64 k0 = kb; k0 < q1; k0 += 32) {
-      const u32 tot = load_chunk(k0);
+      const u32 tot = one_chunk ? tot1 : load_chunk(k0);
       const u32 iters = (tot + 31) & ~31u;
       u32 l2 = 0;
       for (u32 it = lane; it < iters; it += 32) {
