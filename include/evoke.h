@@ -24,8 +24,10 @@
  *    noted (to size internal buffers and to read validation results) and
  *    return after the results are written, unless stated otherwise.
  *  - The caller owns every buffer passed in.  The library allocates its
- *    internal workspace with cudaMallocAsync on `stream` and frees it before
- *    returning.
+ *    internal workspace on `stream` from a memory pool of its own (one per
+ *    device, created on first use) and frees it before returning (plans:
+ *    when destroyed).  Freed memory stays reserved by that pool for later
+ *    calls rather than being unmapped at each synchronisation.
  *  - Return value: EVOKE_OK or one of the error codes below; nothing throws
  *    across the ABI.  evoke_strerror() names a code.
  *  - Counts are int64 two's-complement; the arithmetic wraps modulo 2^64,

@@ -270,6 +270,42 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+// Device memory comes from a pool private to the library, one per device,
+// whose release threshold is unlimited: the blocks of a finished call stay
+// reserved for the next one instead of being unmapped at every stream
+// synchronisation (a 1M-vertex plan holds tens of GB).
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+template <class T>
+cudaError_t dmalloc(T** ptr, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t p = library_pool();
+  void* v = nullptr;
+  const cudaError_t e = p ? cudaMallocFromPoolAsync(&v, bytes, p, st) : cudaMallocAsync(&v, bytes, st);
+  *ptr = static_cast<T*>(v);
+  return e;
+}
+
 // a bump allocator over one cudaMallocAsync block
 struct Arena {
   char* base = nullptr;
@@ -480,7 +516,7 @@ int validate_csr(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, uin
   const u64 S = 2 * m;
   size_t bytes = sz<u32>(S) + sz<int>(4);
   void* blk = nullptr;
-  if (cudaMallocAsync(&blk, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  if (dmalloc(&blk, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   Graph g{};
   g.n = n;
   g.S = S;
@@ -517,7 +553,7 @@ int plan_relabel_setup(evoke_plan* P) {
   if (P->batch || !relabel_wanted() || P->n < 2) return EVOKE_OK;
   cudaStream_t st = P->st;
   u32* d = nullptr;
-  if (cudaMallocAsync(&d, 2 * sizeof(u32), st) != cudaSuccess) return EVOKE_ENOMEM;
+  if (dmalloc(&d, 2 * sizeof(u32), st) != cudaSuccess) return EVOKE_ENOMEM;
   cudaMemsetAsync(d, 0, 2 * sizeof(u32), st);
   degree_max_kernel<<<(P->n + 255) / 256, 256, 0, st>>>(P->rowptr, P->n, d);
   u32 h[2] = {0, 0};
@@ -527,7 +563,7 @@ int plan_relabel_setup(evoke_plan* P) {
   if (h[0] > kRelabelMaxDegree) return EVOKE_OK;  // rows too long for the in-place sort
   const u64 S = 2 * P->m;
   size_t bytes = 3 * sz<u32>(P->n + 1) + sz<u32>(S) + sz<u32>(h[0] + 1);
-  if (cudaMallocAsync(&P->rl_block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  if (dmalloc(&P->rl_block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   Arena ar{static_cast<char*>(P->rl_block), bytes, 0, st};
   P->rl_new_id = ar.take<u32>(P->n + 1);
   P->rl_old_of = ar.take<u32>(P->n + 1);
@@ -555,7 +591,7 @@ int plan_stage1(evoke_plan* P, bool validate) {
                  sz<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1)) + sz<u32>(S) +
                  sz<u64>(S + 1) + sz<int>(4) + sz<u32>(4) + sz<unsigned char>(S);
   if (P->batch) bytes += sz<u32>(n + 1) + sz<u32>(S) + sz<u32>(n);
-  if (cudaMallocAsync(&P->block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  if (dmalloc(&P->block, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   P->bytes = bytes;
   Arena ar{static_cast<char*>(P->block), bytes, 0, st};
   Graph& g = P->g;
@@ -634,7 +670,7 @@ int plan_stage2(evoke_plan* P) {
                  sz<u64>((size_t)NACC * n) + root_scratch_bytes(root_map_stride(map_n), ctas) + 256 * 8 +
                  sz<u32>(n) + sz<u32>(256) + sz<u32>(4) +
                  sz<u32>((size_t)ctas * P->pref_stride) + sz<u32>((size_t)link_warps * 2 * dmax);
-  if (cudaMallocAsync(&P->block2, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  if (dmalloc(&P->block2, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   P->bytes2 = bytes;
   Arena ar{static_cast<char*>(P->block2), bytes, 0, st};
   P->g.tl = ar.take<u32>(P->ntri_entries);
@@ -968,7 +1004,7 @@ int evoke_plan_create_batch(const uint32_t* rowptr_cat, const uint32_t* colidx_c
   // the largest component sizes the per-CTA maps of the root pass
   {
     u32* d = nullptr;
-    if (cudaMallocAsync(&d, sizeof(u32), st) != cudaSuccess) {
+    if (dmalloc(&d, sizeof(u32), st) != cudaSuccess) {
       delete P;
       return EVOKE_ENOMEM;
     }
@@ -1111,7 +1147,7 @@ int evoke_plan_set_model(evoke_plan* plan, const float* params) {
   }
   plan->model = params;
   if (params && !plan->model_block && plan->n) {
-    if (cudaMallocAsync(&plan->model_block, sizeof(float) * 5 * (size_t)plan->n + 256, plan->st) !=
+    if (dmalloc(&plan->model_block, sizeof(float) * 5 * (size_t)plan->n + 256, plan->st) !=
         cudaSuccess)
       return EVOKE_ENOMEM;
     plan->feat = static_cast<float*>(plan->model_block);
@@ -1129,7 +1165,7 @@ int evoke_plan_features(evoke_plan* plan, float* X, void* stream) {
     launch_features(plan->g, plan->acc, X, st);
   } else if (plan->n) {
     float* tmp = nullptr;
-    if (cudaMallocAsync(&tmp, sizeof(float) * 4 * (size_t)plan->n, st) != cudaSuccess) return EVOKE_ENOMEM;
+    if (dmalloc(&tmp, sizeof(float) * 4 * (size_t)plan->n, st) != cudaSuccess) return EVOKE_ENOMEM;
     launch_features(plan->g, plan->acc, tmp, st);
     const u64 cnt = 4 * (u64)plan->n;
     unpermute_rows_kernel<float><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
@@ -1145,7 +1181,7 @@ int evoke_plan_root_timing(evoke_plan* plan, uint64_t* root_cycles, uint64_t* ct
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   u64* cyc = reinterpret_cast<u64*>(root_cycles);
   if (root_cycles && plan->relabel && plan->n &&
-      cudaMallocAsync(&cyc, sizeof(u64) * (size_t)plan->n, st) != cudaSuccess)
+      dmalloc(&cyc, sizeof(u64) * (size_t)plan->n, st) != cudaSuccess)
     return EVOKE_ENOMEM;
   plan->rs.cycles = cyc;
   plan->rs.cta_end = reinterpret_cast<u64*>(cta_end_ns);
@@ -1265,8 +1301,8 @@ int evoke_edge_orbits(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n
     long long* tmp = nullptr;
     u32* orig = nullptr;
     if (P->relabel) {
-      if (cudaMallocAsync(&tmp, sizeof(long long) * S, st) != cudaSuccess ||
-          cudaMallocAsync(&orig, sizeof(u32) * S, st) != cudaSuccess)
+      if (dmalloc(&tmp, sizeof(long long) * S, st) != cudaSuccess ||
+          dmalloc(&orig, sizeof(u32) * S, st) != cudaSuccess)
         rc = EVOKE_ENOMEM;
       else
         launch_orig_slot(P->in_rowptr, P->in_col, P->rl_old_of, P->rl_rowptr, P->rl_col, P->n,
@@ -1306,7 +1342,7 @@ int evoke_edge_orbit_counts(const uint32_t* rowptr, const uint32_t* colidx, uint
   const u64 S = P->g.S;
   if (!rc && S) {
     u32* orig = nullptr;
-    if (P->relabel && cudaMallocAsync(&orig, sizeof(u32) * S, st) != cudaSuccess) rc = EVOKE_ENOMEM;
+    if (P->relabel && dmalloc(&orig, sizeof(u32) * S, st) != cudaSuccess) rc = EVOKE_ENOMEM;
     if (!rc)
       phase("edge_orbits", orig ? 2 : 1, st, [&] {
         if (orig)
@@ -1331,7 +1367,7 @@ int evoke_graphlet_totals(const int64_t* counts, uint32_t n, int32_t orbits, int
   u64 sums[73] = {};
   if (n) {
     u64* dsum = nullptr;
-    if (cudaMallocAsync(&dsum, sizeof(u64) * orbits, st) != cudaSuccess) return EVOKE_ENOMEM;
+    if (dmalloc(&dsum, sizeof(u64) * orbits, st) != cudaSuccess) return EVOKE_ENOMEM;
     cudaMemsetAsync(dsum, 0, sizeof(u64) * orbits, st);
     launch_column_sums(reinterpret_cast<const long long*>(counts), n, orbits, dsum,
                        sm_count_cached(), st);
@@ -1375,7 +1411,7 @@ int evoke_build_dag(const uint32_t* rowptr, const uint32_t* colidx, uint32_t n, 
   size_t bytes = sz<u32>(n) + sz<u32>(S) + sz<u32>(n) + sz<char>(scan_tmp_bytes(std::max<u64>(S, n) + 1)) +
                  sz<u32>(m) + sz<int>(4);
   void* blk = nullptr;
-  if (cudaMallocAsync(&blk, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
+  if (dmalloc(&blk, bytes, st) != cudaSuccess) return EVOKE_ENOMEM;
   Arena ar{static_cast<char*>(blk), bytes, 0, st};
   Graph g{};
   g.n = n;
