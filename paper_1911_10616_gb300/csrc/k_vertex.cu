@@ -1,4 +1,4 @@
-// Neighbour-sum rounds (the O(m+n) class of Tab. orbits-category) and the
+// Neighbour-sum passes (the O(m+n) class of Tab. orbits-category) and the
 // fused equation + induced-transform kernel: the non-induced counts DM of
 // Lem. 4vertexorbit and Thm. 5vertexorbit from the accumulated partial sums,
 // then DIM = A^-1 DM (App. A) by back substitution, written as int64[n x 73].
@@ -13,7 +13,7 @@ __device__ __forceinline__ u64 A(const u64* acc, int idx, u32 n, u32 u) {
 }
 __device__ __forceinline__ u64 sgn(long long x) { return (u64)x; }
 
-// round 1: sums over N(u) of functions of d(v) and T(u,v)
+// neighbour-sum pass 1: sums over N(u) of functions of d(v) and T(u,v)
 __global__ void vsum1_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   const u32 u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -53,7 +53,7 @@ __global__ void vsum1_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   }
 }
 
-// round 2: needs the per-vertex values of round 1, the per-slot edge orbits
+// neighbour-sum pass 2: needs the per-vertex values of pass 1, the per-slot edge orbits
 // and the root / wheel / 4-clique passes
 __global__ void vsum2_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   const u32 u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -144,7 +144,7 @@ __global__ void vsum2_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   put(A_DM14, r[kK4] / 3);
 }
 
-// round 3: sums of round-2 values over N(u)
+// neighbour-sum pass 3: sums of pass-2 values over N(u)
 __global__ void vsum3_kernel(Graph g, u64* __restrict__ acc) {
   const u32 u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -293,7 +293,7 @@ finalize_kernel(Graph g, const u64* __restrict__ acc, long long* __restrict__ ou
   }
 }
 
-// round 2 of the 4-vertex-orbit mode: DM4, DM9, DM12, DM14 only
+// neighbour-sum pass 2 of the 4-vertex-orbit mode: DM4, DM9, DM12, DM14 only
 __global__ void vsum2_four_kernel(Graph g, SlotArrays sa, u64* __restrict__ acc) {
   const u32 u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
