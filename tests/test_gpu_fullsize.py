@@ -49,14 +49,25 @@ def pattern_consistency(oracle_mod, counts):
     return True
 
 
-def run_plan(ev, rp, col, n, m):
+def run_plan(ev, rp, col, n, m, configs=((512, 2, 0, 1),)):
+    """Counts of one plan under each (threads, CTAs per SM, schedule, chunk)
+    configuration of the per-root pass; all must agree bit for bit."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     plan = ev.Plan.single(rp, col, n, m, validate=True)
     out = plan.new_output()
-    plan.set_tuning(512, min(plan.info()["root_ctas"], plan.info()["root_ctas_max"]))
-    plan.execute(out)
-    import torch
-    torch.cuda.synchronize()
-    res = out.cpu().numpy()
+    res = None
+    for th, per_sm, sched, chunk in configs:
+        plan.set_tuning(th, min(sms * per_sm, plan.info()["root_ctas_max"]))
+        plan.set_schedule(sched, chunk)
+        out.fill_(-1)
+        plan.execute(out)
+        plan.status()
+        got = out.cpu().numpy()
+        if res is None:
+            res = got
+        else:
+            assert np.array_equal(got, res), (th, per_sm, sched, chunk)
     plan.destroy()
     return res
 
@@ -64,7 +75,9 @@ def run_plan(ev, rp, col, n, m):
 def test_chung_lu_1m_invariants(ev, oracle_mod):
     g = gg.chung_lu(1_000_000, 10_000_000, 2.1, 5000, 1)
     rp, col = ev.to_device(g)
-    dim = run_plan(ev, rp, col, g.n, g.m)
+    # the configuration the bench settles on (1024-thread CTAs, one per SM,
+    # roots grouped by highest-degree neighbour) and the default one
+    dim = run_plan(ev, rp, col, g.n, g.m, configs=((1024, 1, 1, 16), (512, 2, 0, 1)))
     assert (dim >= 0).all()
     assert np.array_equal(dim[:, 0], g.degrees())
     assert pattern_consistency(oracle_mod, dim)
