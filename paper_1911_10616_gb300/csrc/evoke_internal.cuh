@@ -110,6 +110,24 @@ struct Graph {
 };
 
 // device helpers ------------------------------------------------------------
+// per-warp segmented sum over runs of equal `key` (non-decreasing across the
+// lanes, 0xffffffff for idle lanes); returns the run total on the run's last
+// lane and sets *is_tail there.
+__device__ __forceinline__ u64 seg_sum(u32 key, u64 val, bool* is_tail) {
+  const int lane = threadIdx.x & 31;
+  const u32 prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const u32 heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  const u32 upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  const int start = 31 - __clz(heads & upto);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 y = __shfl_up_sync(0xffffffffu, val, o);
+    if (lane - o >= start) val += y;
+  }
+  *is_tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+  return val;
+}
+
 __device__ __forceinline__ bool prec(const u32* deg, u32 i, u32 j) {
   u32 di = deg[i], dj = deg[j];
   return di < dj || (di == dj && i < j);

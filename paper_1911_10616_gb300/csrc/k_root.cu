@@ -1,6 +1,5 @@
 // Per-root 2-hop pass (Thm. 5vertexorbit, orbits needing W(u,v), TT(u,v) and
-// D(u,v); Thm. 5-Cycle-Clique for orbit 34), the wheel pass (orbits 68, 69)
-// and 5-cliques (orbit 72).
+// D(u,v); Thm. 5-Cycle-Clique for orbit 34) and the orders of its roots.
 //
 // One CTA owns one root u at a time (persistent CTAs pull roots from a queue
 // ordered by decreasing work, the degree-bucket schedule).  Each CTA has a
@@ -118,23 +117,6 @@ __device__ void neighbour_degree_prefix(const Graph& g, u32 ub, u32 du, u32* pre
 template <int kThreads>
 constexpr u32 smem_pref_cap() { return kThreads >= 256 ? 2048u : 512u; }
 
-// per-warp segmented sum over runs of equal `key` (non-decreasing across the
-// lanes, 0xffffffff for idle lanes); returns the run total on the run's last
-// lane and sets *is_tail there.
-__device__ __forceinline__ u64 seg_sum(u32 key, u64 val, bool* is_tail) {
-  const int lane = threadIdx.x & 31;
-  const u32 prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const u32 heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
-  const u32 upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  const int start = 31 - __clz(heads & upto);
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u64 y = __shfl_up_sync(0xffffffffu, val, o);
-    if (lane - o >= start) val += y;
-  }
-  *is_tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  return val;
-}
 
 template <int kThreads>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads)
@@ -554,323 +536,6 @@ __global__ void sched_scatter_kernel(const u64* __restrict__ work, u32 n, u32* c
   if (u < n) order[atomicAdd(&cursor[63u - bucket_of(work[u])], 1u)] = u;
 }
 
-// --- wheel pass: 4-cycles inside N(u) per vertex, for every slot (u,a) -------
-// (orbits 68 and 69: a wheel is a hub u plus a 4-cycle of the link graph
-// G[N(u)], whose edges are the triangle-list entries of u's slots).  Each
-// 4-cycle of G[N(u)] is found once, from its top vertex a, the smallest id
-// (the highest degree after the relabelling): the wedges a - b - c with b > a
-// and c > a give W'(a,c) = |{b > a : b ~ a, b ~ c}|, and C(W'(a,c), 2) cycles
-// have top a and opposite vertex c.  They are credited to a and to c, and the
-// middle b of each wedge a - b - c gets W'(a,c) - 1 (one per other middle), so
-// every slot (u,x) ends with the number of 4-cycles of G[N(u)] through x.
-// Ordering the tops by degree is what keeps the wedge count down: a wedge
-// through a hub b is walked only from the few tops of still higher degree.
-// One warp per slot (u,a): it walks the b > a entries of tl(u,a) 32 at a time
-// and, for each, the tail c > a of tl(u,b) (entered by binary search; slot
-// order = id order).  Sweep 1 counts W' in 16-bit halves of shared-memory
-// words when d(u) <= kLinkSmem (then W' < 2^16), else in 32-bit words of the
-// warp's global scratch row, and lists the touched partners; sweep 2 walks
-// the same wedges again to credit the middles.
-constexpr int kLinkWarps = 8;
-constexpr u32 kLinkSmem = 2048;
-
-constexpr size_t kLinkDynSmem = (size_t)kLinkWarps * (kLinkSmem / 2 + kLinkSmem) * sizeof(u32);
-
-__global__ void __launch_bounds__(kLinkWarps * 32)
-link_kernel(Graph g, SlotArrays sa, u32* __restrict__ scratch, u32 dmax) {
-  extern __shared__ u32 link_smem[];
-  u32 (*s_map)[kLinkSmem / 2] = reinterpret_cast<u32 (*)[kLinkSmem / 2]>(link_smem);
-  u32 (*s_list)[kLinkSmem] =
-      reinterpret_cast<u32 (*)[kLinkSmem]>(link_smem + (size_t)kLinkWarps * (kLinkSmem / 2));
-  __shared__ u32 s_pref[kLinkWarps][33];
-  __shared__ u64 s_start[kLinkWarps][32];
-  __shared__ u32 s_sb[kLinkWarps][32];
-  __shared__ u32 s_cnt[kLinkWarps];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 gw = blockIdx.x * kLinkWarps + wid;
-  const u32 nwarps = gridDim.x * kLinkWarps;
-  u32* gmap = scratch + (u64)gw * 2 * dmax;
-  u32* glist = gmap + dmax;
-  for (u32 i = lane; i < kLinkSmem / 2; i += 32) s_map[wid][i] = 0;
-  __syncwarp();
-  for (u64 s = gw; s < g.S; s += nwarps) {
-    if (sa.T[s] < 2) continue;
-    const u64 q1 = g.tl_ptr[s + 1];
-    u64 kb = g.tl_ptr[s];
-    {  // first entry of tl(u,a) with b > a
-      u64 hi = q1;
-      while (kb < hi) {
-        const u64 mid = kb + ((hi - kb) >> 1);
-        if (g.tl[mid] <= (u32)s) kb = mid + 1;
-        else hi = mid;
-      }
-    }
-    if (q1 - kb < 2) continue;  // a cycle with top a needs two middles
-    const u32 lo = g.col[g.rev[s]];  // the row owning slot s
-    const u32 ub = g.rowptr[lo], du = g.rowptr[lo + 1] - ub;
-    const bool small = du <= kLinkSmem;
-    u32* list = small ? s_list[wid] : glist;
-    if (lane == 0) s_cnt[wid] = 0;
-    __syncwarp();
-    // the wedges of 32 b's at a time: per lane one b (slot sb, tail start
-    // and length), then the concatenated tails one entry per lane
-    auto load_chunk = [&](u64 k0) -> u32 {
-      const u64 k = k0 + lane;
-      u32 len = 0, sb = 0;
-      u64 st0 = 0;
-      if (k < q1) {
-        sb = g.tl[k];
-        u64 l2 = g.tl_ptr[sb], h2 = g.tl_ptr[sb + 1];
-        const u64 end = h2;
-        while (l2 < h2) {  // first partner slot > s
-          const u64 mid = l2 + ((h2 - l2) >> 1);
-          if (g.tl[mid] <= (u32)s) l2 = mid + 1;
-          else h2 = mid;
-        }
-        st0 = l2;
-        len = (u32)(end - l2);
-      }
-      u32 incl = len;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      s_pref[wid][lane + 1] = incl;
-      if (lane == 0) s_pref[wid][0] = 0;
-      s_start[wid][lane] = st0;
-      s_sb[wid][lane] = sb;
-      __syncwarp();
-      return s_pref[wid][32];
-    };
-    auto next_list = [&](u32 it, u32& l2) {  // l2: list of entry it (non-decreasing)
-      if (s_pref[wid][l2 + 1] <= it) {
-        u32 h2 = 32;
-        ++l2;
-        while (h2 - l2 > 1) {
-          const u32 mid = (l2 + h2) >> 1;
-          if (s_pref[wid][mid] <= it) l2 = mid;
-          else h2 = mid;
-        }
-      }
-    };
-    // sweep 1: W' per partner c, and the cycles with top a
-    u64 c4 = 0;
-    u32 tot1 = 0;  // entries of the (last) chunk
-    for (u64 k0 = kb; k0 < q1; k0 += 32) {
-      const u32 tot = load_chunk(k0);
-      tot1 = tot;
-      u32 l2 = 0;
-      for (u32 it = lane; it < tot; it += 32) {
-        next_list(it, l2);
-        const u32 pc = g.tl[s_start[wid][l2] + (it - s_pref[wid][l2])] - ub;
-        u32 old;
-        if (small) {
-          const u32 sh = (pc & 1u) * 16u;
-          old = (atomicAdd(&s_map[wid][pc >> 1], 1u << sh) >> sh) & 0xffffu;
-        } else {
-          old = atomicAdd(&gmap[pc], 1u);
-        }
-        c4 += old;
-        if (old == 0) list[atomicAdd(&s_cnt[wid], 1u)] = pc;
-      }
-      __syncwarp();
-    }
-    // opposite vertices: C(W'(a,c), 2) each
-    const u32 cnt = s_cnt[wid];
-    for (u32 i = lane; i < cnt; i += 32) {
-      const u32 pc = list[i];
-      u32 w;
-      if (small) {
-        const u32 sh = (pc & 1u) * 16u;
-        w = (s_map[wid][pc >> 1] >> sh) & 0xffffu;
-      } else {
-        w = gmap[pc];
-      }
-      if (w >= 2) atomicAdd(&sa.b68[ub + pc], (u64)w * (w - 1) / 2);
-    }
-    // sweep 2: each middle b of a wedge a - b - c gets W'(a,c) - 1.  With one
-    // chunk only, its tables are still in shared memory from sweep 1.
-    const bool one_chunk = q1 - kb <= 32;
-    for (u64 k0 = kb; k0 < q1; k0 += 32) {
-      const u32 tot = one_chunk ? tot1 : load_chunk(k0);
-      const u32 iters = (tot + 31) & ~31u;
-      u32 l2 = 0;
-      for (u32 it = lane; it < iters; it += 32) {
-        u32 key = 0xffffffffu;
-        u64 add = 0;
-        if (it < tot) {
-          next_list(it, l2);
-          const u32 pc = g.tl[s_start[wid][l2] + (it - s_pref[wid][l2])] - ub;
-          u32 w;
-          if (small) {
-            const u32 sh = (pc & 1u) * 16u;
-            w = (s_map[wid][pc >> 1] >> sh) & 0xffffu;
-          } else {
-            w = gmap[pc];
-          }
-          key = l2;
-          add = w - 1;
-        }
-        bool tail;
-        const u64 sum = seg_sum(key, add, &tail);
-        if (tail && key != 0xffffffffu && sum) atomicAdd(&sa.b68[s_sb[wid][key]], sum);
-      }
-      __syncwarp();
-    }
-    __syncwarp();
-    for (u32 i = lane; i < cnt; i += 32) {
-      const u32 pc = list[i];
-      if (small) s_map[wid][pc >> 1] = 0;
-      else gmap[pc] = 0;
-    }
-    __syncwarp();
-    c4 = warp_sum(c4);
-    if (lane == 0 && c4) atomicAdd(&sa.b68[s], c4);
-  }
-}
-
-// --- 5-cliques: per DAG edge (a -> b), triangles inside S = N+(a)^N+(b) ----
-// Every 5-clique a<b<c<d<e (DAG order) is seen once, at its lowest edge (a,b),
-// as the triangle {c,d,e} of G[S].  One warp per DAG edge: S goes to shared
-// memory (ascending ids), the adjacency inside S to bitmap rows, and the
-// triangles of G[S] through c are sum_{d in row(c)} popc(row(c) & row(d)) / 2.
-// Edges whose S exceeds the shared-memory capacity take a slower path that
-// re-derives S on the fly.
-constexpr int kK5Warps = 4;
-
-__device__ void k5_slow_edge(const Graph& g, u64* acc, u32 a, u32 b) {
-  const int lane = threadIdx.x & 31;
-  const u32 n = g.n;
-  const u32 ab = g.dag_ptr[a], ae = g.dag_ptr[a + 1];
-  const u32 bb = g.dag_ptr[b], be = g.dag_ptr[b + 1];
-  u64 cab = 0;
-  for (u32 i = ab + lane; i < ae; i += 32) {
-    const u32 c = g.dag_col[i];
-    if (!contains_u32(g.dag_col, bb, be, c)) continue;
-    u64 cc = 0;
-    const u32 cb = g.dag_ptr[c], ce = g.dag_ptr[c + 1];
-    for (u32 p = cb; p < ce; ++p) {
-      const u32 d = g.dag_col[p];
-      if (!contains_u32(g.dag_col, ab, ae, d) || !contains_u32(g.dag_col, bb, be, d)) continue;
-      u64 cd = 0;
-      for (u32 p2 = g.dag_ptr[d]; p2 < g.dag_ptr[d + 1]; ++p2) {
-        const u32 f = g.dag_col[p2];
-        if (contains_u32(g.dag_col, cb, ce, f) && contains_u32(g.dag_col, ab, ae, f) &&
-            contains_u32(g.dag_col, bb, be, f)) {
-          ++cd;
-          atomicAdd(&acc[(u64)A_K5 * n + f], 1ull);
-        }
-      }
-      if (cd) atomicAdd(&acc[(u64)A_K5 * n + d], cd);
-      cc += cd;
-    }
-    if (cc) atomicAdd(&acc[(u64)A_K5 * n + c], cc);
-    cab += cc;
-  }
-  cab = warp_sum(cab);
-  if (lane == 0 && cab) {
-    atomicAdd(&acc[(u64)A_K5 * n + a], cab);
-    atomicAdd(&acc[(u64)A_K5 * n + b], cab);
-  }
-}
-
-__global__ void __launch_bounds__(kK5Warps * 32)
-k5_kernel(Graph g, u64* __restrict__ acc, u32 m, u32 smax) {
-  extern __shared__ u32 k5_smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const u32 words = (smax + 31) / 32;
-  u32* S = k5_smem + (size_t)wid * (2 * smax + (size_t)smax * words);
-  u32* tcnt = S + smax;
-  u32* rows = tcnt + smax;
-  const u32 n = g.n;
-  const u32 gw = blockIdx.x * kK5Warps + wid;
-  const u32 nw = gridDim.x * kK5Warps;
-  for (u32 e = gw; e < m; e += nw) {
-    const u32 a = g.col[g.rev[g.dag_slot[e]]], b = g.dag_col[e];  // source, target of DAG edge e
-    u32 xb = g.dag_ptr[a], xe = g.dag_ptr[a + 1];
-    u32 yb = g.dag_ptr[b], ye = g.dag_ptr[b + 1];
-    if (xe - xb < 3 || ye - yb < 3) continue;
-    if (xe - xb > ye - yb) {  // walk the shorter list
-      u32 t = xb; xb = yb; yb = t;
-      t = xe; xe = ye; ye = t;
-    }
-    // S = N+(a) ^ N+(b), ascending
-    u32 s = 0;
-    bool over = false;
-    for (u32 base = xb; base < xe; base += 32) {
-      const u32 i = base + lane;
-      const u32 x = i < xe ? g.dag_col[i] : 0;
-      const bool hit = i < xe && contains_u32(g.dag_col, yb, ye, x);
-      const u32 bal = __ballot_sync(0xffffffffu, hit);
-      const u32 pos = s + __popc(bal & ((1u << lane) - 1u));
-      if (hit && pos < smax) S[pos] = x;
-      s += __popc(bal);
-    }
-    if (s < 3) continue;
-    if (s > smax) over = true;
-    if (over) {
-      k5_slow_edge(g, acc, a, b);
-      continue;
-    }
-    const u32 w = (s + 31) / 32;
-    for (u32 i = lane; i < s * w; i += 32) rows[i] = 0;
-    __syncwarp();
-    // adjacency inside S (both directions)
-    for (u32 ci = lane; ci < s; ci += 32) {
-      const u32 c = S[ci];
-      for (u32 p = g.dag_ptr[c]; p < g.dag_ptr[c + 1]; ++p) {
-        const u32 d = g.dag_col[p];
-        const u32 di = lower_bound_u32(S, 0, s, d);
-        if (di < s && S[di] == d) {
-          atomicOr(&rows[ci * w + (di >> 5)], 1u << (di & 31));
-          atomicOr(&rows[di * w + (ci >> 5)], 1u << (ci & 31));
-        }
-      }
-    }
-    __syncwarp();
-    // per unordered edge (c,d) of G[S], c < d: k_cd = |N_S(c) ^ N_S(d)|
-    // triangles; crediting k_cd to both ends gives each vertex twice its
-    // triangle count
-    for (u32 ci = lane; ci < s; ci += 32) tcnt[ci] = 0;
-    __syncwarp();
-    for (u32 ci = lane; ci < s; ci += 32) {
-      const u32* rc = rows + ci * w;
-      u32 tc = 0;
-      for (u32 k = (ci + 1) >> 5; k < w; ++k) {
-        u32 bits = rc[k];
-        if (k == (ci >> 5)) bits &= ~((2u << (ci & 31)) - 1u);  // partners d > c
-        while (bits) {
-          const u32 di = k * 32 + __ffs(bits) - 1;
-          bits &= bits - 1;
-          const u32* rd = rows + di * w;
-          u32 kcd = 0;
-          for (u32 q = 0; q < w; ++q) kcd += __popc(rc[q] & rd[q]);
-          if (kcd) {
-            tc += kcd;
-            atomicAdd(&tcnt[di], kcd);
-          }
-        }
-      }
-      if (tc) atomicAdd(&tcnt[ci], tc);
-    }
-    __syncwarp();
-    u64 tot = 0;
-    for (u32 ci = lane; ci < s; ci += 32) {
-      const u32 t2 = tcnt[ci];
-      const u32 tc = t2 >> 1;
-      if (tc) atomicAdd(&acc[(u64)A_K5 * n + S[ci]], (u64)tc);
-      tot += tc;
-    }
-    tot = warp_sum(tot);
-    if (lane == 0 && tot) {
-      atomicAdd(&acc[(u64)A_K5 * n + a], tot / 3);
-      atomicAdd(&acc[(u64)A_K5 * n + b], tot / 3);
-    }
-    __syncwarp();
-  }
-}
-
 }  // namespace
 
 u32 root_map_stride(u32 map_n) {
@@ -997,38 +662,3 @@ void root_configure() {
   root_dyn_smem<1024>(1);
 }
 
-void link_configure() {
-  cudaFuncSetAttribute(link_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinkDynSmem);
-}
-
-void launch_link(const Graph& g, const SlotArrays& sa, u32* scratch, u32 warps, u32 dmax,
-                 cudaStream_t st) {
-  if (!g.S || !warps) return;
-  link_kernel<<<warps / kLinkWarps, kLinkWarps * 32, kLinkDynSmem, st>>>(g, sa, scratch, dmax);
-}
-
-K5Config k5_configure(u32 max_outdeg) {
-  K5Config c{};
-  if (max_outdeg < 3) return c;
-  // shared memory per warp: S list + |S| x ceil(|S|/32) bitmap words
-  u32 smax = (max_outdeg + 31) / 32 * 32;
-  const u32 cap = 640;
-  if (smax > cap) smax = cap;
-  const size_t per_warp = (2 * (size_t)smax + (size_t)smax * ((smax + 31) / 32)) * sizeof(u32);
-  c.smem = per_warp * kK5Warps;
-  c.smax = smax;
-  cudaFuncSetAttribute(k5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5_kernel, kK5Warps * 32, c.smem);
-  c.blocks = (u32)sms * (u32)(per_sm > 0 ? per_sm : 1) * 4;
-  return c;
-}
-
-void launch_k5(const Graph& g, u64* acc, const K5Config& c, cudaStream_t st) {
-  const u32 m = (u32)(g.S / 2);
-  if (!m || !c.blocks) return;
-  k5_kernel<<<c.blocks, kK5Warps * 32, c.smem, st>>>(g, acc, m, c.smax);
-}
