@@ -605,7 +605,10 @@ def run_learned(args, rank, world, dist, barrier):
             plan.execute(out)
         _lib.profile_reset()
         _lib.profile_enable(True)
-        t = timed(lambda: plan.execute_profiled(out), args.steps, stream, barrier)
+        launches0 = _lib.launch_count()
+        with ClockSampler(local_device()) as clk:
+            t = timed(lambda: plan.execute_profiled(out), args.steps, stream, barrier)
+        launches = _lib.launch_count() - launches0
         _lib.profile_enable(False)
         ph = _lib.profile_read()
         cyc, ends = plan.root_timing(out)
@@ -613,7 +616,8 @@ def run_learned(args, rank, world, dist, barrier):
         res[name] = {"ms_per_step": 1000.0 * t / args.steps,
                      "root_ms": ph["root"][2] / max(ph["root"][1], 1),
                      "tail_ms": float((e.max() - e.min()) / 1e6),
-                     "cycles": cyc.cpu().numpy()}
+                     "cycles": cyc.cpu().numpy(), "phases": ph, "launches": launches,
+                     "clocks": clk.summary()}
     X, y, _ = learned.measure(g)
     pred = _lib.mlp_forward(X, params).cpu().numpy()
     meas = y.cpu().numpy()
@@ -630,6 +634,14 @@ def run_learned(args, rank, world, dist, barrier):
     plan.destroy()
     if rank != 0:
         return None
+    roof = roofline_of(res["learned"]["phases"], g, ev, rp, col, n, m, args)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = cpu_oracle_baseline(args.workload, seed=1, budget_s=args.cpu_budget)
+            cpu.pop("seconds", None)
+        except Exception as exc:  # report, never fake
+            cpu = {"error": repr(exc)}
     t_l = res["learned"]["ms_per_step"] / 1000.0
     return {
         "metric": metric_of(spec), "value": world * m / t_l, "unit": UNIT,
@@ -643,14 +655,19 @@ def run_learned(args, rank, world, dist, barrier):
         "learned_vs_degree_bucket": {
             "step_speedup": res["degree_bucket"]["ms_per_step"] / res["learned"]["ms_per_step"],
             "root_pass_speedup": res["degree_bucket"]["root_ms"] / res["learned"]["root_ms"],
-            "degree_bucket": {k: v for k, v in res["degree_bucket"].items() if k != "cycles"},
-            "learned": {k: v for k, v in res["learned"].items() if k != "cycles"},
+            "degree_bucket": {k: v for k, v in res["degree_bucket"].items()
+                              if k in ("ms_per_step", "root_ms", "tail_ms")},
+            "learned": {k: v for k, v in res["learned"].items()
+                        if k in ("ms_per_step", "root_ms", "tail_ms")},
             "spearman_log2_cycles": {"learned": learned.spearman(pred[busy], meas[busy]),
                                      "wedge_work": learned.spearman(work[busy], meas[busy])},
             "mae_log2_cycles": {"learned": float(np.abs(pred[busy] - meas[busy]).mean()),
                                 "wedge_work_affine": float(np.abs(A @ coef - meas[busy]).mean())},
             "simulated_makespan_over_lower_bound": sim},
-        "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+        "e2e": None, "gpu_launches": res["learned"]["launches"], "roofline": roof,
+        "phases_ms": {k2: round(v[2] / max(v[1], 1), 3)
+                      for k2, v in sorted(res["learned"]["phases"].items())},
+        "cpu_baseline": cpu, "clocks": res["learned"]["clocks"],
     }
 
 
