@@ -26,7 +26,8 @@ def test_list_schedule_makespan():
     # two workers, longest first: {5, 2, 1} and {3, 3, 2} -> 8
     assert learned.list_schedule_makespan(c, np.argsort(-c, kind="stable"), 2) == 8.0
     # the bad order the learned model is compared against: shortest first
-    assert learned.list_schedule_makespan(c, np.argsort(c, kind="stable"), 2) == 9.0
+    # A: 1, 2, 3 -> 6; B: 2, 3, 5 -> 10
+    assert learned.list_schedule_makespan(c, np.argsort(c, kind="stable"), 2) == 10.0
 
 
 def test_wedge_work_is_sum_of_neighbour_degrees():
