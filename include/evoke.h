@@ -18,7 +18,9 @@
  *    rowptr[n] = 2m) and colidx[2m] (uint32).  Each row must be strictly
  *    increasing, without self-loops, and the graph symmetric (a simple
  *    undirected graph; Sec. 2).  n < 2^32 - 1 and 2m < 2^32.  Isolated
- *    vertices and n = 0 are legal.
+ *    vertices and n = 0 are legal.  The largest degree must be at most
+ *    65,535 (EVOKE_ERANGE otherwise): the per-pair counts of the 2-hop pass
+ *    are 32-bit, and their bounds (d, d(d-1)/2, d^2) fit only up to there.
  *  - `stream` is a cudaStream_t (0 = legacy default stream).  Work is
  *    enqueued on it; the functions synchronise that stream internally where
  *    noted (to size internal buffers and to read validation results) and
@@ -46,7 +48,7 @@ extern "C" {
 #define EVOKE_OK 0
 #define EVOKE_EINVAL 1       /* bad argument (null pointer, sizes inconsistent) */
 #define EVOKE_ENOTSIMPLE 2   /* input is not a simple undirected graph (validate) */
-#define EVOKE_ERANGE 3       /* a vertex id >= n (validate) or n / m too large */
+#define EVOKE_ERANGE 3       /* a vertex id >= n (validate), n / m too large, or a degree > 65,535 */
 #define EVOKE_ENOMEM 4       /* internal device allocation failed */
 #define EVOKE_ECUDA 5        /* a CUDA call or kernel launch failed */
 #define EVOKE_ETIMEOUT 6     /* a bounded device wait gave up */

@@ -646,6 +646,7 @@ int plan_stage1(evoke_plan* P, bool validate) {
   P->ntri_entries = total;
   P->dmax = mx[0];
   P->max_outdeg = mx[1];
+  if (P->dmax > kMaxDegree) return EVOKE_ERANGE;  // 32-bit per-pair counts could wrap
   return EVOKE_OK;
 }
 

@@ -261,6 +261,11 @@ void launch_k4_known(const Graph& g, const SlotArrays& sa, u64* acc, u64 total, 
 void launch_union_csr(const u32* rowptr_cat, const u32* col_cat, const long long* vtx_off,
                       const long long* edge_off, u32 G, u32 n, u64 S, u32* rowptr, u32* col,
                       u32* comp_base, cudaStream_t st);
+// Largest vertex degree accepted.  The per-pair records of the root pass keep
+// 32-bit counts whose bounds follow from the degree d: W <= d, D <= C(W, 2)
+// and the 3-path sums Y, X <= d^2 all stay below 2^32 for d <= 65,535 (the
+// per-pair 3-path count P has its own overflow flag).
+constexpr u32 kMaxDegree = 65535;
 // relabelling by decreasing degree (single graphs)
 constexpr u32 kRelabelMaxDegree = 32768;  // longest row the block sort holds in shared memory
 u32 relabel_prepare(const u32* rowptr, u32 n, u32 dmax, u32* hist, u32* new_id, u32* old_of,
