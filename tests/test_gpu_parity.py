@@ -146,3 +146,17 @@ def test_hub_grouped_schedule(ev, oracle_mod):
     plan.launch_graph(out)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_degree_limit(ev):
+    # degrees above 65,535 could wrap the 2-hop pass's 32-bit per-pair counts:
+    # plans refuse them with EVOKE_ERANGE instead
+    g = gg.star(70_000)
+    rp, col = ev.to_device(g)
+    with pytest.raises(ev.EvokeError) as info:
+        ev.count_orbits(rp, col, g.n, g.m)
+    assert info.value.code == 3
+    h = gg.star(65_535)  # the largest accepted degree
+    rp, col = ev.to_device(h)
+    out = ev.count_orbits(rp, col, h.n, h.m).cpu().numpy()
+    assert out[0, 0] == 65_535 and out[0, 7] == 65_535 * 65_534 * 65_533 // 6
