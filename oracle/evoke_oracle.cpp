@@ -27,6 +27,20 @@
 //       induced counts DIM = A^-1 DM (App. A), A derived by brute force over
 //       the patterns themselves.
 //
+// Also: the edge orbits E0..E11 of Fig. edge_orbits, by the Definition that
+// follows the figure (brute force over non-induced copies, tiny graphs) and
+// by Lem. 4edgeorbit from the base counts; and the 4-vertex orbits alone
+// (the method stopped after Lem. 4vertexorbit).
+//
+// Pins (the tests' CPU suite): the 4-vertex block of A equals Fig. A (one
+// printed entry is an erratum, see there) and its inverse Fig. Ainv; the
+// orbits equal networkx's automorphism classes; brute force equals an
+// independent networkx enumeration and closed forms (cliques, stars, cycles,
+// paths); every DM equation equals non-induced brute force; the formula path
+// equals brute force on random graphs; edge orbits: hand counts, closed forms,
+// brute force = lemma, and totals against the vertex-orbit brute force; the
+// 4-vertex-only path equals brute force and the full method's first columns.
+//
 // Arithmetic is exact: __int128 accumulation; a value outside int64 raises the
 // overflow flag (return code 7).  Where the printed equations are garbled the
 // reading taken is stated at the equation (see the comments marked READING).
