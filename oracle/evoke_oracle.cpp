@@ -32,8 +32,9 @@
 // by Lem. 4edgeorbit from the base counts; and the 4-vertex orbits alone
 // (the method stopped after Lem. 4vertexorbit).
 //
-// Pins (the tests' CPU suite): the 4-vertex block of A equals Fig. A (one
-// printed entry is an erratum, see there) and its inverse Fig. Ainv; the
+// Pins (the tests' CPU suite): the 4-vertex block of A equals Fig. A (but for
+// one printed entry, A[5][13], an erratum: the definition gives 4) and its
+// inverse Fig. Ainv; the
 // orbits equal networkx's automorphism classes; brute force equals an
 // independent networkx enumeration and closed forms (cliques, stars, cycles,
 // paths); every DM equation equals non-induced brute force; the formula path
