@@ -21,7 +21,7 @@ namespace {
 // warp's global scratch row, and lists the touched partners; sweep 2 walks
 // the same wedges again to credit the middles.
 constexpr int kLinkWarps = 8;
-constexpr u32 kLinkSmem = 1024;
+constexpr u32 kLinkSmem = 512;
 
 constexpr size_t kLinkDynSmem = (size_t)kLinkWarps * (kLinkSmem / 2 + kLinkSmem) * sizeof(u32);
 
